@@ -1,0 +1,57 @@
+"""Brute force for tiny inputs (test infrastructure only).
+
+Straight from the definitions, with no cleverness at all:
+
+* LCA(x, y): of all common ancestors of x and y (a node is its own ancestor),
+  the one furthest from the root (Sec. 3, problem statement).
+* bridge: an edge whose deletion increases the number of connected components
+  (Sec. 4, problem statement); counted by a BFS over the graph without it.
+"""
+
+from __future__ import annotations
+
+from collections import deque
+
+
+def ancestors(parent, x):
+    """Path from x up to the root, x first."""
+    out = [x]
+    while parent[out[-1]] != -1:
+        out.append(int(parent[out[-1]]))
+        if len(out) > len(parent):
+            raise ValueError("parent array has a cycle")
+    return out
+
+
+def lca(parent, x, y):
+    ax = ancestors(parent, int(x))
+    common = set(ax) & set(ancestors(parent, int(y)))
+    return max(common, key=lambda z: len(ancestors(parent, z)))
+
+
+def components(n, edges, skip=-1):
+    adj = [[] for _ in range(n)]
+    for e, (a, b) in enumerate(edges):
+        if e != skip:
+            adj[int(a)].append(int(b))
+            adj[int(b)].append(int(a))
+    seen = [False] * n
+    count = 0
+    for s in range(n):
+        if seen[s]:
+            continue
+        count += 1
+        seen[s] = True
+        dq = deque([s])
+        while dq:
+            x = dq.popleft()
+            for w in adj[x]:
+                if not seen[w]:
+                    seen[w] = True
+                    dq.append(w)
+    return count
+
+
+def bridges(n, edges):
+    base = components(n, edges)
+    return [int(components(n, edges, skip=e) > base) for e in range(len(edges))]
