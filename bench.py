@@ -1,0 +1,451 @@
+#!/usr/bin/env python3
+"""Benchmark of the Euler-tour hot path on one GB300 (or N, one process each).
+
+One step = the whole path over one batch of synthetic inputs:
+  * LCA at scale: three trees of n = 2^24 nodes (grasp unlimited, 1024 and 1,
+    labels permuted), each preprocessed (Euler tour, list ranking, preorder /
+    depth / size, sparse table) and then asked 2^24 uniform queries;
+  * bridges: a small-diameter graph (n = 2^22, m = 2^25 - 1) and a
+    large-diameter graph (n = 2^22, m = 2^22 - 1 + 2^24, 2^16 planted cuts).
+value = (LCA queries + bridge edges) per second over the device-timed steps,
+inputs resident in HBM. Per-part rates are in "breakdown".
+
+--impl reference times the CPU oracle (test infrastructure, single thread) on
+a bounded sample of the same workload; it is the reference arm of this
+benchmark. With torchrun (N > 1) every rank runs its own replica of the
+workload (weak scaling, no data-path collective); rank 0 prints the line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "LCA queries/s + bridge edges/s"
+UNIT = "(queries+edges)/s"
+TREES = [(1 << 24, None), (1 << 24, 1024), (1 << 24, 1)]
+Q = 1 << 24
+GRAPHS = [("easy", 1 << 22, (1 << 25) - 1), ("hard", 1 << 22, (1 << 22) - 1 + (1 << 24))]
+WORKLOAD = ("LCA: 3 trees n=2^24 (grasp inf, 1024, 1; permuted labels) x (preprocess + 2^24 uniform queries); "
+            "bridges: easy n=2^22 m=2^25-1, hard n=2^22 m=2^22-1+2^24 (2^16 planted cuts)")
+SMALL_TREES = [(1 << 16, None)]
+SMALL_Q = 1 << 16
+SMALL_GRAPHS = [("easy", 1 << 14, 1 << 17), ("hard", 1 << 14, (1 << 14) - 1 + (1 << 16))]
+
+# algorithmic bytes per unit for each phase (what the method must read and write
+# once: int32 = 4 B); keys are (phase, part) where part is "tree" or "graph"
+ALGO = {
+    ("rank.walk0", "tree"): ("arc", 12),       # read succ 4, write (sublist, offsets) 8
+    ("rank.walk0", "graph"): ("arc", 12),
+    ("rmq.level_min", "tree"): ("node", 8),    # read level l-1, write level l
+    ("rmq.level_min", "graph"): ("pos", 8),
+    ("rmq.level_max", "graph"): ("pos", 8),
+    ("lca.query", "tree"): ("query", 32),      # u, v 8; pre 8; two table entries 8; order 4; out 4
+    ("sort.scatter", "tree"): ("node", 16),    # read key, value; write key, value
+    ("sort.scatter", "graph"): ("arc", 16),
+    ("lca.node_stats", "tree"): ("node", 32),  # read 2 packed 16, gather 2 prefixes 4, write 3x4, order 4 (approx)
+    ("lca.parent_pre", "tree"): ("node", 16),
+    ("br.hook", "graph"): ("edge", 17),        # edge 8, flag 1, two root lookups 8
+    ("br.lowhigh_prep", "graph"): ("edge", 24),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--small", action="store_true", help="small sizes (functional check only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_inputs(small: bool, seed: int):
+    import synth
+    trees = SMALL_TREES if small else TREES
+    q = SMALL_Q if small else Q
+    graphs = SMALL_GRAPHS if small else GRAPHS
+    tr = []
+    for n, grasp in trees:
+        parent = synth.tree_parent(n, grasp, seed=seed)
+        u, v = synth.lca_queries(n, q, seed=seed)
+        tr.append(dict(n=n, grasp=grasp, parent=parent, u=u, v=v))
+    gr = []
+    for kind, n, m in graphs:
+        if kind == "easy":
+            e = synth.easy_graph(n, m, seed=seed)
+        else:
+            e = synth.hard_graph(n, m - (n - 1), max(1, n // 64), seed=seed)
+        gr.append(dict(kind=kind, n=n, m=m, edges=e))
+    return tr, gr
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+
+    import paper_2103_15217_gb300 as etl
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    etl.build()
+    etl.load_library()
+    trees, graphs = make_inputs(args.small, seed=1 + rank)
+
+    d_trees = [dict(t, parent_d=torch.from_numpy(t["parent"]).to(dev), u_d=torch.from_numpy(t["u"]).to(dev),
+                    v_d=torch.from_numpy(t["v"]).to(dev)) for t in trees]
+    d_graphs = [dict(g, edges_d=torch.from_numpy(g["edges"]).to(dev)) for g in graphs]
+    units = sum(t["u"].shape[0] for t in trees) + sum(g["m"] for g in graphs)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step(record):
+        """One pass of the whole path; record(name) drops an event on the stream."""
+        outs = []
+        for t in d_trees:
+            record(f"tree{len(outs)}.start")
+            h = etl.lca_preprocess(t["parent_d"])
+            record(f"tree{len(outs)}.pre")
+            out = h.query(t["u_d"], t["v_d"])
+            record(f"tree{len(outs)}.query")
+            h.free()
+            outs.append(out)
+        for g in d_graphs:
+            record(f"graph.{g['kind']}.start")
+            outs.append(etl.find_bridges(g["edges_d"], g["n"]))
+            record(f"graph.{g['kind']}.end")
+        return outs
+
+    def timed_step(profile=False):
+        evs = {}
+
+        def rec(name):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            evs[name] = e
+        step(rec)
+        return evs
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        timed_step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed steps (per-part events; L2 flushed between steps)
+    etl.profile_reset()
+    etl.profile_enable(True)
+    launches0 = etl.launch_count()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    steps = []
+    for _ in range(args.steps):
+        flush.zero_()
+        steps.append(timed_step())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = etl.launch_count() - launches0
+    etl.profile_enable(False)
+    phases = etl.profile_read()
+
+    def el(evs, a, b):
+        return evs[a].elapsed_time(evs[b]) / 1e3
+
+    part = {}
+    step_s = []
+    for evs in steps:
+        tot = 0.0
+        for i, t in enumerate(trees):
+            pre = el(evs, f"tree{i}.start", f"tree{i}.pre")
+            qry = el(evs, f"tree{i}.pre", f"tree{i}.query")
+            part.setdefault(f"tree{i}.pre", []).append(pre)
+            part.setdefault(f"tree{i}.query", []).append(qry)
+            tot += pre + qry
+        for g in graphs:
+            b = el(evs, f"graph.{g['kind']}.start", f"graph.{g['kind']}.end")
+            part.setdefault(f"graph.{g['kind']}", []).append(b)
+            tot += b
+        step_s.append(tot)
+    t_step = sum(step_s) / len(step_s)
+    if world > 1:
+        tt = torch.tensor([t_step], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = units * world / t_step
+
+    breakdown = {}
+    for i, t in enumerate(trees):
+        pre = statistics.mean(part[f"tree{i}.pre"])
+        qry = statistics.mean(part[f"tree{i}.query"])
+        g = "inf" if t["grasp"] is None else str(t["grasp"])
+        breakdown[f"lca_grasp_{g}"] = {
+            "n": t["n"], "q": int(t["u"].shape[0]), "preprocess_ms": pre * 1e3, "query_ms": qry * 1e3,
+            "preprocess_nodes_per_s": t["n"] / pre, "queries_per_s": t["u"].shape[0] / qry,
+            "queries_per_s_incl_preprocess": t["u"].shape[0] / (pre + qry)}
+    for g in graphs:
+        b = statistics.mean(part[f"graph.{g['kind']}"])
+        breakdown[f"bridges_{g['kind']}"] = {"n": g["n"], "m": g["m"], "ms": b * 1e3, "edges_per_s": g["m"] / b}
+
+    roofline = roofline_from_phases(phases, trees, graphs, args.steps)
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, etl, trees, graphs, dev, units, world)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded generators of the paper's tree and graph "
+        "families; the bridge datasets of Table 1 are stood in for by the easy/hard generators)",
+        "config": {"workload": WORKLOAD if not args.small else "small functional check", "units_per_step": units,
+                   "l2": "flushed between steps (512 MB write) and working set >> L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "wall_s_timed": wall},
+        "breakdown": breakdown,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in sorted(phases.items())},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        result["cpu_baseline"] = cpu_baseline(small=args.small)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return result if rank == 0 else None
+
+
+def roofline_from_phases(phases, trees, graphs, steps):
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    # dominant phase by total device time
+    name, (ms, launches) = max(phases.items(), key=lambda kv: kv[1][0])
+    # units per launch: phases shared by the tree and the graph parts are split by launch count
+    n_tree = len(trees)
+    per_step = launches / steps
+    tree_units = {"node": sum(t["n"] for t in trees) / n_tree, "arc": sum(2 * t["n"] for t in trees) / n_tree,
+                  "query": sum(t["u"].shape[0] for t in trees) / n_tree}
+    graph_units = {"edge": sum(g["m"] for g in graphs) / len(graphs),
+                   "arc": sum(2 * g["n"] - 1 for g in graphs) / len(graphs),
+                   "pos": sum(2 * g["n"] - 1 for g in graphs) / len(graphs)}
+    part = "tree" if (name, "tree") in ALGO else "graph"
+    key = (name, part)
+    if key not in ALGO:
+        return {"bound": "hbm", "kernel": name, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                "traffic": None, "note": "no algorithmic byte count for this phase"}
+    unit, bpu = ALGO[key]
+    if (name, "graph") in ALGO and (name, "tree") in ALGO:
+        units = (n_tree * tree_units[ALGO[(name, "tree")][0]] * ALGO[(name, "tree")][1] +
+                 len(graphs) * graph_units[ALGO[(name, "graph")][0]] * ALGO[(name, "graph")][1]) / (n_tree + len(graphs))
+        bytes_per_launch = units
+    else:
+        bytes_per_launch = (tree_units if part == "tree" else graph_units)[unit] * bpu
+    if name.startswith("rmq.level"):  # one launch per level; bytes above are per level
+        pass
+    avg_s = ms / 1e3 / launches
+    achieved = bytes_per_launch / avg_s / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}
+
+
+def run_e2e(args, etl, trees, graphs, dev, units, world):
+    import torch
+    stream = torch.cuda.current_stream()
+    h_trees = [dict(parent=torch.from_numpy(t["parent"]).pin_memory(), u=torch.from_numpy(t["u"]).pin_memory(),
+                    v=torch.from_numpy(t["v"]).pin_memory(),
+                    out=torch.empty(t["u"].shape[0], dtype=torch.int32).pin_memory(), n=t["n"]) for t in trees]
+    h_graphs = [dict(edges=torch.from_numpy(g["edges"]).pin_memory(),
+                     out=torch.empty(g["m"], dtype=torch.uint8).pin_memory(), n=g["n"]) for g in graphs]
+    h2d = sum(t["parent"].numel() * 4 + t["u"].numel() * 8 for t in h_trees) + sum(g["edges"].numel() * 4 for g in h_graphs)
+    d2h = sum(t["out"].numel() * 4 for t in h_trees) + sum(g["out"].numel() for g in h_graphs)
+
+    def one():
+        for t in h_trees:
+            p = t["parent"].to(dev, non_blocking=True)
+            u = t["u"].to(dev, non_blocking=True)
+            v = t["v"].to(dev, non_blocking=True)
+            h = etl.lca_preprocess(p)
+            t["out"].copy_(h.query(u, v), non_blocking=True)
+            h.free()
+        for g in h_graphs:
+            e = g["edges"].to(dev, non_blocking=True)
+            g["out"].copy_(etl.find_bridges(e, g["n"]), non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3 / args.steps
+    return {"value": units * world / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": t * 1e3}
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+
+def oracle_sample(small: bool):
+    """A bounded sample of the workload for the single-threaded CPU oracle."""
+    import synth
+    if small:
+        n, q, gn, gm = 1 << 12, 1 << 12, 1 << 11, 1 << 13
+    else:
+        n, q, gn, gm = 1 << 21, 1 << 21, 1 << 19, 1 << 22
+    parent = synth.tree_parent(n, None, seed=9)
+    u, v = synth.lca_queries(n, q, seed=9)
+    easy = synth.easy_graph(gn, gm, seed=9)
+    hard = synth.hard_graph(gn, gm - (gn - 1), max(1, gn // 64), seed=9)
+    desc = (f"oracle: Euler tour + Tarjan offline LCA on a random recursive tree n={n}, q={q}; "
+            f"DFS low-function bridges on easy and hard graphs n={gn}, m={gm}")
+    return parent, u, v, easy, hard, gn, desc
+
+
+def run_oracle_once(sample):
+    import oracle
+    parent, u, v, easy, hard, gn, _ = sample
+    t0 = time.perf_counter()
+    oracle.tree_tour(parent)
+    oracle.lca_offline(parent, u, v)
+    oracle.bridges_dfs(gn, easy)
+    oracle.bridges_dfs(gn, hard)
+    dt = time.perf_counter() - t0
+    units = u.shape[0] + easy.shape[0] + hard.shape[0]
+    return units, dt
+
+
+def cpu_baseline(small: bool):
+    sample = oracle_sample(small)
+    units, dt = run_oracle_once(sample)
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample[-1],
+            "seconds": dt, "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    sample = oracle_sample(args.small)
+    for _ in range(args.warmup):
+        run_oracle_once(sample)
+    tot_units, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        u, t = run_oracle_once(sample)
+        tot_units += u
+        tot_t += t
+    value = tot_units / tot_t
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample[-1]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample[-1]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * etl.h -- C ABI of the GB300 (sm_103a) Euler-tour library.
+ *
+ * The library computes, on one GPU, the Euler tour technique of "Euler Meets
+ * GPU: Practical Graph Algorithms with Theoretical Guarantees" (Polak,
+ * Siwiec, Stobierski; arXiv 2103.15217) and its two applications:
+ * lowest common ancestors by range-minimum queries over the tour, and bridges
+ * by the Tarjan-Vishkin method.
+ *
+ * Common rules for every entry point below:
+ *  - Array arguments are DEVICE pointers (cudaMalloc / torch CUDA memory) in
+ *    the caller's current CUDA context, unless a comment says otherwise; all
+ *    integers are little-endian int32 unless stated. Inputs are read-only;
+ *    outputs are written completely. The caller owns every array it passes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Every call only enqueues work on that stream and returns; it
+ *    never synchronises unless its comment says so. Device memory the call
+ *    needs for itself is taken with cudaMallocAsync / cudaFreeAsync on that
+ *    same stream.
+ *  - The return value reports what the host can see at call time: ETL_EINVAL
+ *    for bad sizes or null pointers (nothing is enqueued then), ETL_ENOMEM /
+ *    ETL_ECUDA for a failed allocation or launch. Errors in the DATA (a parent
+ *    array that is not one tree, an id out of range, an exhausted iteration
+ *    cap) are only known on the device: they are written as an etl_status code
+ *    into a device int32 "status word" (first error wins; 0 = ok) and the
+ *    affected outputs are set to -1 (LCA) or 0 (bridge mask). Every device loop
+ *    whose trip count depends on the data has a cap, so no input makes a
+ *    kernel spin.
+ *  - Concurrency: calls on different streams may overlap; a preprocessed LCA
+ *    handle is read-only for queries, so queries on several streams may run
+ *    at once.
+ */
+#ifndef ETL_H
+#define ETL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum etl_status {
+    ETL_OK = 0,
+    ETL_EINVAL = 1,     /* bad argument seen on the host; nothing enqueued */
+    ETL_ENOMEM = 2,     /* device allocation failed */
+    ETL_ECUDA = 3,      /* a CUDA call or launch failed */
+    ETL_EBADTREE = 4,   /* parent array is not exactly one rooted tree on all n nodes */
+    ETL_EBADQUERY = 5,  /* a query id outside [0, n) */
+    ETL_EBADGRAPH = 6,  /* an edge endpoint outside [0, n) */
+    ETL_ETIMEOUT = 7    /* a capped device loop ran out (malformed or adversarial input) */
+} etl_status;
+
+/* Human-readable name of a status code (static string). */
+const char *etl_status_string(int32_t status);
+
+/* ------------------------------------------------------------------ list ranking
+ * List ranking (Sec. 2.2, "Using an Euler Tour on GPU"): for a singly linked
+ * list stored as succ[0..len) (succ[e] = next element, -1 at the tail) that
+ * starts at element `head`, writes rank[e] = distance of e from the head
+ * (rank[head] = 0). All len elements must lie on the one list; otherwise
+ * `status` (device int32, may be NULL) receives ETL_EBADTREE and the ranks of
+ * the unreachable elements are unspecified. This is the ruling-set ranker
+ * that the tree and bridge paths use internally, exposed for reuse.
+ * len in [1, 2^31 - 2]; head in [0, len).
+ */
+etl_status etl_list_rank(const int32_t *succ, int64_t len, int32_t head, int32_t *rank, int32_t *status,
+                         void *stream);
+
+/* ------------------------------------------------------------------ LCA
+ * Lowest common ancestors (Sec. 3): preprocessing builds the Euler tour of the
+ * tree (Sec. 2.1, successor = next(twin)), ranks it once (Sec. 2.2), derives
+ * preorder, depth and subtree size from the ranks, and builds a sparse table
+ * for range-minimum queries over the preorder sequence (the RMQ reduction of
+ * Sec. 3.1). A query is then answered in O(1) with two table reads.
+ *
+ * Opaque handle; it owns the device arrays of one preprocessed tree.
+ */
+typedef struct etl_lca_s *etl_lca_t;
+
+/*
+ * lca_preprocess: parent[0..n) with parent[root] = -1 and every other entry in
+ * [0, n) describes one rooted tree (the input format of Sec. 3.2). n in
+ * [1, 2^30]. On success *out receives a new handle (host memory, owned by the
+ * caller until lca_free). The handle's tables are being built asynchronously
+ * on `stream`; queries enqueued on the same stream see them, queries on
+ * another stream must wait for it (event or synchronisation). Data errors go
+ * to the handle's status word (see lca_status). Children are visited in
+ * ascending label order, so the preorder numbering is unique.
+ */
+etl_status lca_preprocess(const int32_t *parent, int32_t n, void *stream, etl_lca_t *out);
+
+/*
+ * lca_query: out[i] = LCA(u[i], v[i]) for i in [0, q), for the tree of h
+ * (Sec. 3, problem statement: the deepest node that is an ancestor of both,
+ * a node being its own ancestor). Ids outside [0, n) give out[i] = -1 and
+ * ETL_EBADQUERY in *status (device int32, may be NULL; written only on error,
+ * never cleared, so several query calls may share it). If the handle holds a
+ * malformed tree every answer is -1. q in [0, 2^40]; u, v, out may not alias.
+ */
+etl_status lca_query(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q, int32_t *out,
+                     int32_t *status, void *stream);
+
+/*
+ * lca_status: waits for the stream the handle was built on, then writes the
+ * handle's data status (an etl_status code, 0 = the tree was valid) to the
+ * HOST int32 *status. Synchronising.
+ */
+etl_status lca_status(etl_lca_t h, int32_t *status);
+
+/*
+ * lca_arrays: device pointers (owned by the handle, valid until lca_free) to
+ * the per-node results of preprocessing, each int32[n]: pre (preorder number,
+ * root 0, children in ascending label order), depth (root 0), size (nodes in
+ * the subtree), order (order[pre[v]] = v). Any output pointer may be NULL.
+ */
+etl_status lca_arrays(etl_lca_t h, const int32_t **pre, const int32_t **depth, const int32_t **size,
+                      const int32_t **order);
+
+/*
+ * lca_export: copies (device to device, on `stream`, ordered after the
+ * handle's own stream only if it is the same stream) the per-node arrays of
+ * lca_arrays into caller-owned int32[n] device arrays; any may be NULL.
+ */
+etl_status lca_export(etl_lca_t h, int32_t *pre, int32_t *depth, int32_t *size, int32_t *order, void *stream);
+
+/* lca_free: releases the handle and its device memory (stream-ordered on the
+ * handle's stream, which must still exist). NULL is accepted. */
+etl_status lca_free(etl_lca_t h);
+
+/* ------------------------------------------------------------------ bridges
+ * find_bridges: Tarjan-Vishkin bridge finding (Sec. 4.1). edges[0..2m) holds
+ * m undirected edges as (u0, v0, u1, v1, ...), ids in [0, n); self-loops and
+ * parallel edges are allowed and the graph may be disconnected. Writes
+ * is_bridge[e] = 1 if deleting edge e increases the number of connected
+ * components, else 0. Phases: a spanning forest from a hook-and-compress
+ * connected-components pass (an edge whose hook succeeds is a forest edge),
+ * the Euler tour of that forest, per-vertex minimum / maximum over non-forest
+ * neighbours, subtree low / high by range-minimum / -maximum queries over the
+ * tour, and the test: forest edge {u, parent(u)} is a bridge iff no
+ * non-forest edge leaves the subtree of u. Endpoints out of range give
+ * ETL_EBADGRAPH in *status (device int32, may be NULL; the call first sets it
+ * to 0) and an all-zero mask.
+ * n in [1, 2^30], m in [0, 2^31 - 2].
+ */
+etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
+                        void *stream);
+
+/* ------------------------------------------------------------------ phase timers
+ * Opt-in device timing of the library's own launch groups (not part of the
+ * method; used by the benchmark). When enabled, each launch group is
+ * bracketed by two CUDA events on its stream (skipped while the stream is
+ * being captured into a graph). etl_profile_count / etl_profile_get wait for
+ * the recorded events and aggregate per phase name: total milliseconds and
+ * number of launches. Process-wide; thread-safe.
+ */
+etl_status etl_profile_enable(int32_t on);
+etl_status etl_profile_reset(void);
+etl_status etl_profile_count(int32_t *count);
+etl_status etl_profile_get(int32_t i, char *name, int32_t name_len, double *total_ms, int64_t *launches);
+/* Number of kernels this process has launched through the library so far (host-side counter). */
+etl_status etl_launch_count(int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ETL_H */

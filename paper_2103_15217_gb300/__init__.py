@@ -1,0 +1,211 @@
+"""Python binding of the GB300 Euler-tour library (``include/etl.h``).
+
+Thin ctypes marshalling over ``_build/libetl.so``: every step of the path runs
+in the library's CUDA kernels; PyTorch only provides device memory and the
+current stream. There is no fallback: if the library is not built, or a
+tensor is not a CUDA int32 tensor, the call raises.
+
+    import paper_2103_15217_gb300 as etl
+    h = etl.lca_preprocess(parent)          # parent: int32 CUDA tensor, root = -1
+    out = h.query(u, v)                     # LCA per query pair
+    mask = etl.find_bridges(edges, n)       # edges: (m, 2) int32 CUDA tensor
+    rank = etl.list_rank(succ, head)
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libetl.so")
+
+STATUS = {0: "ETL_OK", 1: "ETL_EINVAL", 2: "ETL_ENOMEM", 3: "ETL_ECUDA", 4: "ETL_EBADTREE",
+          5: "ETL_EBADQUERY", 6: "ETL_EBADGRAPH", 7: "ETL_ETIMEOUT"}
+EXPORTS = ("etl_status_string", "etl_list_rank", "lca_preprocess", "lca_query", "lca_status", "lca_arrays",
+           "lca_export", "lca_free", "find_bridges", "etl_profile_enable", "etl_profile_reset",
+           "etl_profile_count", "etl_profile_get", "etl_launch_count")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class EtlError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} returned {STATUS.get(code, code)}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a) if its sources changed."""
+    import importlib
+    return importlib.import_module(__name__ + ".build").build(force=force)
+
+
+def load_library(path: str | None = None):
+    """Load (once) and declare the C ABI. Raises if the library is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build the CUDA library first (paper_2103_15217_gb300.build())")
+        lib = ctypes.CDLL(p)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        lib.etl_status_string.argtypes = [i32]
+        lib.etl_status_string.restype = ctypes.c_char_p
+        lib.etl_list_rank.argtypes = [P, i64, i32, P, P, P]
+        lib.lca_preprocess.argtypes = [P, i32, P, PP]
+        lib.lca_query.argtypes = [P, P, P, i64, P, P, P]
+        lib.lca_status.argtypes = [P, ctypes.POINTER(i32)]
+        lib.lca_arrays.argtypes = [P, PP, PP, PP, PP]
+        lib.lca_export.argtypes = [P, P, P, P, P, P]
+        lib.lca_free.argtypes = [P]
+        lib.find_bridges.argtypes = [P, i64, i32, P, P, P]
+        lib.etl_launch_count.argtypes = [ctypes.POINTER(i64)]
+        lib.etl_profile_enable.argtypes = [i32]
+        lib.etl_profile_reset.argtypes = []
+        lib.etl_profile_count.argtypes = [ctypes.POINTER(i32)]
+        lib.etl_profile_get.argtypes = [i32, ctypes.c_char_p, i32, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(i64)]
+        for f in EXPORTS[1:]:
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(fn: str, rc: int):
+    if rc != 0:
+        raise EtlError(fn, rc)
+
+
+def _dev_i32(t: torch.Tensor, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous int32 CUDA tensor")
+    return t.data_ptr()
+
+
+def _status_ptr(status) -> int | None:
+    if status is None:
+        return None
+    return _dev_i32(status, "status")
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def new_status(device=None) -> torch.Tensor:
+    """A zeroed device status word (int32[1])."""
+    return torch.zeros(1, dtype=torch.int32, device=device or "cuda")
+
+
+def list_rank(succ: torch.Tensor, head: int, status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """rank[e] = distance of element e from ``head`` along ``succ`` (-1 = end)."""
+    lib = load_library()
+    p = _dev_i32(succ, "succ")
+    rank = torch.empty_like(succ)
+    _check("etl_list_rank", lib.etl_list_rank(p, succ.numel(), int(head), rank.data_ptr(), _status_ptr(status),
+                                              _stream(stream)))
+    return rank
+
+
+class Lca:
+    """A preprocessed tree: wraps an ``etl_lca_t`` handle."""
+
+    def __init__(self, parent: torch.Tensor, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.n = parent.numel()
+        self._h = ctypes.c_void_p()
+        self._stream = _stream(stream)
+        _check("lca_preprocess", lib.lca_preprocess(_dev_i32(parent, "parent"), self.n, self._stream,
+                                                    ctypes.byref(self._h)))
+        self._parent_ref = parent  # keep the input alive until preprocessing has run
+
+    def query(self, u: torch.Tensor, v: torch.Tensor, out: torch.Tensor | None = None,
+              status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if u.numel() != v.numel():
+            raise ValueError("u and v must have the same length")
+        if out is None:
+            out = torch.empty_like(u)
+        _check("lca_query", self._lib.lca_query(self._h, _dev_i32(u, "u"), _dev_i32(v, "v"), u.numel(),
+                                                _dev_i32(out, "out"), _status_ptr(status), _stream(stream)))
+        return out
+
+    def status(self) -> int:
+        st = ctypes.c_int32(-1)
+        _check("lca_status", self._lib.lca_status(self._h, ctypes.byref(st)))
+        return st.value
+
+    def arrays(self, stream=None) -> dict:
+        """Copies of the per-node arrays: pre, depth, size, order (int32[n])."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = {k: torch.empty(self.n, dtype=torch.int32, device=dev) for k in ("pre", "depth", "size", "order")}
+        _check("lca_export", self._lib.lca_export(self._h, out["pre"].data_ptr(), out["depth"].data_ptr(),
+                                                  out["size"].data_ptr(), out["order"].data_ptr(),
+                                                  _stream(stream)))
+        return out
+
+    def free(self):
+        if self._h:
+            self._lib.lca_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def profile_enable(on: bool = True):
+    """Turn the library's per-phase CUDA-event timers on or off."""
+    _check("etl_profile_enable", load_library().etl_profile_enable(1 if on else 0))
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    c = ctypes.c_int64(0)
+    _check("etl_launch_count", load_library().etl_launch_count(ctypes.byref(c)))
+    return c.value
+
+
+def profile_reset():
+    _check("etl_profile_reset", load_library().etl_profile_reset())
+
+
+def profile_read() -> dict:
+    """{phase: (total_ms, launches)} accumulated since the last reset (waits for the events)."""
+    lib = load_library()
+    cnt = ctypes.c_int32(0)
+    _check("etl_profile_count", lib.etl_profile_count(ctypes.byref(cnt)))
+    out = {}
+    buf = ctypes.create_string_buffer(64)
+    for i in range(cnt.value):
+        ms, k = ctypes.c_double(0), ctypes.c_int64(0)
+        _check("etl_profile_get", lib.etl_profile_get(i, buf, 64, ctypes.byref(ms), ctypes.byref(k)))
+        out[buf.value.decode()] = (ms.value, k.value)
+    return out
+
+
+def lca_preprocess(parent: torch.Tensor, stream=None) -> Lca:
+    return Lca(parent, stream)
+
+
+def find_bridges(edges: torch.Tensor, n: int, status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """uint8 mask, 1 for every bridge of the undirected multigraph (m, 2)."""
+    lib = load_library()
+    if edges.dim() != 2 or edges.shape[1] != 2:
+        raise ValueError("edges must have shape (m, 2)")
+    m = edges.shape[0]
+    mask = torch.empty(m, dtype=torch.uint8, device=edges.device)
+    _check("find_bridges", lib.find_bridges(_dev_i32(edges, "edges"), m, int(n), mask.data_ptr(),
+                                            _status_ptr(status), _stream(stream)))
+    return mask

@@ -1,0 +1,54 @@
+// Shared host helpers and the generic list-ranking entry point.
+#include <mutex>
+
+#include "etl_internal.cuh"
+
+namespace etl {
+
+int num_sms() {
+    static std::mutex mu;
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> g(mu);
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+}  // namespace etl
+
+using namespace etl;
+
+extern "C" const char *etl_status_string(int32_t status) {
+    switch (status) {
+        case ETL_OK: return "ETL_OK";
+        case ETL_EINVAL: return "ETL_EINVAL";
+        case ETL_ENOMEM: return "ETL_ENOMEM";
+        case ETL_ECUDA: return "ETL_ECUDA";
+        case ETL_EBADTREE: return "ETL_EBADTREE";
+        case ETL_EBADQUERY: return "ETL_EBADQUERY";
+        case ETL_EBADGRAPH: return "ETL_EBADGRAPH";
+        case ETL_ETIMEOUT: return "ETL_ETIMEOUT";
+        default: return "ETL_UNKNOWN";
+    }
+}
+
+extern "C" etl_status etl_list_rank(const int32_t *succ, int64_t len, int32_t head, int32_t *rank, int32_t *status,
+                                    void *stream) {
+    if (!succ || !rank || len < 1 || len > int64_t(INT32_MAX) - 1 || head < 0 || head >= len) return ETL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    int32_t *d_head = ws.get<int32_t>(1);
+    int32_t *st = status ? status : ws.get<int32_t>(1);
+    if (!ws.ok()) return ETL_ENOMEM;
+    etl_status rc = set_device_i32(d_head, head, s);
+    RankResult rr{};
+    if (!rc) rc = list_rank(succ, len, nullptr, d_head, false, len, st, ws, &rr);
+    if (!rc) rc = final_rank(rr, len, rank, s);
+    return rc;
+}

@@ -1,0 +1,382 @@
+// Bridges by the Tarjan-Vishkin method (Sec. 4.1) on one GPU.
+//
+// Phase 1, spanning forest: a lock-free hook-and-compress connected-components
+//   pass in the style the paper takes from Jaiganesh and Burtscher: every edge
+//   finds the roots of its two ends (with path halving) and hooks the larger
+//   root under the smaller one with a CAS. A CAS that succeeds joins two
+//   different trees, so its edge is a forest edge; exactly n - c succeed.
+// Phase 2, Euler tour of the forest (Sec. 2.1): forest edge t owns half-edges
+//   2t = (u_t, v_t) and 2t+1 = (v_t, u_t), so twin(a) = a ^ 1. A stable radix
+//   sort by tail groups the half-edges of every vertex (array B); next(a) is
+//   the following entry of B with the same tail, cyclically; succ(a) =
+//   next(twin(a)). Each component's cyclic list is cut in front of the first
+//   half-edge of its root (the smallest vertex, which is where hooking ends),
+//   and the component lists are chained into one list behind a virtual head,
+//   which is ranked once (rank.cu).
+// Phase 3, low / high: with tin(x) = rank of the half-edge entering x (a root
+//   gets the position just before its component), the subtree of u is the
+//   tour interval [tin(u), tout(u)], tout(u) = rank of the half-edge leaving
+//   u. nlo(x) / nhi(x) = min / max of tin(x) and tin(w) over non-forest
+//   edges (x, w), by atomics (the paper uses a segmented reduction);
+//   placed at tin(x) in tour order, low(u) / high(u) are range-min / -max
+//   queries over [tin(u), tout(u)] (sparse tables, rmq.cu).
+// Phase 4, the test: forest edge {u, parent(u)} is a bridge iff
+//   low(u) >= tin(u) and high(u) <= tout(u), i.e. no non-forest edge leaves
+//   the subtree of u. (Sec. 4.1 states the condition the other way round;
+//   "at least one of low, high outside the subtree" is the NON-bridge case,
+//   since such an edge reconnects the subtree with the rest of the graph.)
+#include <climits>
+
+#include "etl_internal.cuh"
+
+namespace etl {
+namespace {
+
+constexpr int64_t kFindCap = int64_t(1) << 26;  // bound on pointer-chasing steps of one edge
+
+__global__ void k_init(int32_t n, int32_t *__restrict__ par, int32_t *__restrict__ first_pos,
+                       int32_t *__restrict__ tin) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        par[v] = int32_t(v);
+        first_pos[v] = -1;
+        tin[v] = 0;
+    }
+}
+
+// root of x with path halving; -1 if the step budget runs out
+__device__ __forceinline__ int32_t find_root(int32_t *par, int32_t x, int64_t &budget) {
+    while (budget-- > 0) {
+        const int32_t p = __ldcg(par + x);
+        if (p == x) return x;
+        const int32_t gp = __ldcg(par + p);
+        if (gp == p) return p;
+        par[x] = gp;  // only non-roots are rewritten, always to a smaller id
+        x = gp;
+    }
+    return -1;
+}
+
+__global__ void k_hook(const int32_t *__restrict__ edges, int64_t m, int32_t n, int32_t *__restrict__ par,
+                       uint8_t *__restrict__ is_tree, int32_t *__restrict__ status) {
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        uint8_t tree = 0;
+        if (a < 0 || a >= n || b < 0 || b >= n) {
+            set_status(status, ETL_EBADGRAPH);
+        } else {
+            int64_t budget = kFindCap;
+            while (true) {
+                const int32_t ra = find_root(par, a, budget), rb = find_root(par, b, budget);
+                if (ra < 0 || rb < 0) {
+                    set_status(status, ETL_ETIMEOUT);
+                    break;
+                }
+                if (ra == rb) break;
+                const int32_t hi = max(ra, rb), lo = min(ra, rb);
+                if (atomicCAS(par + hi, hi, lo) == hi) {
+                    tree = 1;
+                    break;
+                }
+                a = ra;  // someone hooked one of the roots meanwhile: retry from them
+                b = rb;
+            }
+        }
+        is_tree[e] = tree;
+    }
+}
+
+__global__ void k_compress(int32_t n, int32_t *__restrict__ par, int32_t *__restrict__ status) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        int64_t budget = kFindCap;
+        const int32_t r = find_root(par, int32_t(v), budget);
+        if (r < 0)
+            set_status(status, ETL_ETIMEOUT);
+        else
+            par[v] = r;
+    }
+}
+
+// forest edges packed in edge order: tuv[2t] = u, tuv[2t+1] = v, tedge[t] = e
+__global__ void k_forest_edges(const int32_t *__restrict__ edges, int64_t m, const uint8_t *__restrict__ is_tree,
+                               const int32_t *__restrict__ tpos, int32_t *__restrict__ tuv,
+                               int32_t *__restrict__ tedge, int32_t *__restrict__ n_arcs) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_arcs = 2 * tpos[m];
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        if (is_tree[e]) {
+            const int32_t t = tpos[e];
+            tuv[2 * t] = edges[2 * e];
+            tuv[2 * t + 1] = edges[2 * e + 1];
+            tedge[t] = int32_t(e);
+        }
+    }
+}
+
+// first / one-past-last position of each tail in the sorted half-edge array
+__global__ void k_group_bounds(const int32_t *__restrict__ key, const int32_t *__restrict__ d_len,
+                               int32_t *__restrict__ first_pos, int32_t *__restrict__ end_pos) {
+    const int64_t len = *d_len;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < len; i += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t k = key[i];
+        if (i == 0 || key[i - 1] != k) first_pos[k] = int32_t(i);
+        if (i == len - 1 || key[i + 1] != k) end_pos[k] = int32_t(i + 1);
+    }
+}
+
+// succ(twin(b)) := next(b) for every half-edge b at position i of B; half-edge
+// slots beyond the forest (and the virtual head, set later) are inert
+__global__ void k_forest_succ(const int32_t *__restrict__ key, const int32_t *__restrict__ B,
+                              const int32_t *__restrict__ d_len, int64_t cap, const int32_t *__restrict__ first_pos,
+                              const int32_t *__restrict__ end_pos, int32_t *__restrict__ succ) {
+    const int64_t len = *d_len;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cap; i += int64_t(gridDim.x) * blockDim.x) {
+        if (i < len) {
+            const int32_t b = B[i], x = key[i];
+            const int32_t nb = (i + 1 < end_pos[x]) ? B[i + 1] : B[first_pos[x]];
+            succ[b ^ 1] = nb;
+        } else {
+            succ[i] = ETL_END;
+        }
+    }
+}
+
+__global__ void k_root_flags(int32_t n, const int32_t *__restrict__ par, const int32_t *__restrict__ first_pos,
+                             uint8_t *__restrict__ flag) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        flag[v] = (par[v] == v && first_pos[v] >= 0) ? 1 : 0;
+}
+
+__global__ void k_root_list(int32_t n, const uint8_t *__restrict__ flag, const int32_t *__restrict__ rpos,
+                            int32_t *__restrict__ roots) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        if (flag[v]) roots[rpos[v]] = int32_t(v);
+}
+
+// cut each component's cyclic tour in front of its root's first half-edge and
+// chain the components: virtual head -> comp 0 -> comp 1 -> ... -> end
+__global__ void k_chain(int32_t n, const int32_t *__restrict__ rpos, const int32_t *__restrict__ roots,
+                        const int32_t *__restrict__ B, const int32_t *__restrict__ first_pos,
+                        const int32_t *__restrict__ end_pos, int32_t vhead, int32_t *__restrict__ succ) {
+    const int32_t c = rpos[n];
+    if (blockIdx.x == 0 && threadIdx.x == 0) succ[vhead] = c > 0 ? B[first_pos[roots[0]]] : ETL_END;
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < c; k += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t r = roots[k];
+        const int32_t tail = B[end_pos[r] - 1] ^ 1;  // the half-edge whose successor was the head
+        succ[tail] = (k + 1 < c) ? B[first_pos[roots[k + 1]]] : ETL_END;
+    }
+}
+
+// tour positions of forest edges: the half-edge ranked first goes down into the child
+__global__ void k_forest_tin(RankResult rr, const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ tuv,
+                             int32_t *__restrict__ tin, int32_t *__restrict__ child, int32_t *__restrict__ etin,
+                             int32_t *__restrict__ etout) {
+    const int64_t T = *d_arcs / 2;
+    const uint4 *pk = reinterpret_cast<const uint4 *>(rr.packed);
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
+        const uint4 q = pk[t];
+        if (q.x >= rr.rcap || q.z >= rr.rcap) {  // cannot happen for a forest built above; keep memory safe
+            child[t] = 0;
+            etin[t] = etout[t] = -1;
+            continue;
+        }
+        const int32_t r0 = rank_of(rr, make_uint2(q.x, q.y)), r1 = rank_of(rr, make_uint2(q.z, q.w));
+        const int32_t c = r0 < r1 ? tuv[2 * t + 1] : tuv[2 * t];
+        const int32_t a = min(r0, r1), b = max(r0, r1);
+        tin[c] = a;
+        child[t] = c;
+        etin[t] = a;
+        etout[t] = b;
+    }
+}
+
+__global__ void k_root_tin(int32_t n, const int32_t *__restrict__ rpos, const int32_t *__restrict__ roots,
+                           const int32_t *__restrict__ B, const int32_t *__restrict__ first_pos, RankResult rr,
+                           int32_t *__restrict__ tin) {
+    const int32_t c = rpos[n];
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < c; k += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t r = roots[k];
+        const uint2 p = rr.packed[B[first_pos[r]]];
+        tin[r] = p.x < rr.rcap ? rank_of(rr, p) - 1 : -1;
+    }
+}
+
+__global__ void k_nlo_init(int32_t n, const int32_t *__restrict__ tin, int32_t *__restrict__ nlo,
+                           int32_t *__restrict__ nhi) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t x = tin[v];
+        nlo[v] = x;
+        nhi[v] = x;
+    }
+}
+
+__global__ void k_nontree_minmax(const int32_t *__restrict__ edges, int64_t m, int32_t n,
+                                 const uint8_t *__restrict__ is_tree, const int32_t *__restrict__ tin,
+                                 int32_t *__restrict__ nlo, int32_t *__restrict__ nhi) {
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        if (is_tree[e]) continue;
+        const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        if (a < 0 || a >= n || b < 0 || b >= n || a == b) continue;
+        const int32_t ta = __ldg(tin + a), tb = __ldg(tin + b);
+        atomicMin(nlo + a, tb);
+        atomicMax(nhi + a, tb);
+        atomicMin(nlo + b, ta);
+        atomicMax(nhi + b, ta);
+    }
+}
+
+// nlo / nhi of every non-root vertex at its tour position; identities at the
+// positions of half-edges going up and at the virtual head (position 0)
+__global__ void k_place(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ child,
+                        const int32_t *__restrict__ etin, const int32_t *__restrict__ etout,
+                        const int32_t *__restrict__ nlo, const int32_t *__restrict__ nhi, int64_t P,
+                        int32_t *__restrict__ L, int32_t *__restrict__ H) {
+    const int64_t T = *d_arcs / 2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        L[0] = INT_MAX;
+        H[0] = INT_MIN;
+    }
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t c = child[t], a = etin[t], b = etout[t];
+        if (a < 0 || b >= P || a >= b) continue;
+        L[a] = nlo[c];
+        H[a] = nhi[c];
+        L[b] = INT_MAX;
+        H[b] = INT_MIN;
+    }
+}
+
+__global__ void k_bridge_test(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ etin,
+                              const int32_t *__restrict__ etout, const int32_t *__restrict__ Lt,
+                              const int32_t *__restrict__ Ht, int64_t P, uint8_t *__restrict__ tflag) {
+    const int64_t T = *d_arcs / 2;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t a = etin[t], b = etout[t];
+        if (a < 0 || b >= P || a >= b) {
+            tflag[t] = 0;
+            continue;
+        }
+        const int32_t low = sparse_query<false>(Lt, P, a, b);
+        const int32_t high = sparse_query<true>(Ht, P, a, b);
+        tflag[t] = (low >= a && high <= b) ? 1 : 0;
+    }
+}
+
+__global__ void k_finalize(int64_t m, const uint8_t *__restrict__ is_tree, const int32_t *__restrict__ tpos,
+                           const uint8_t *__restrict__ tflag, const int32_t *__restrict__ status,
+                           uint8_t *__restrict__ is_bridge) {
+    const bool bad = *status != 0;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x)
+        is_bridge[e] = (!bad && is_tree[e]) ? tflag[tpos[e]] : 0;
+}
+
+int grid_for(int64_t work, int threads) {
+    int64_t blocks = ceil_div(work, threads);
+    const int64_t cap = int64_t(num_sms()) * (2048 / threads) * 4;
+    if (blocks > cap) blocks = cap;
+    return int(blocks < 1 ? 1 : blocks);
+}
+
+}  // namespace
+}  // namespace etl
+
+using namespace etl;
+
+extern "C" etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
+                                   void *stream) {
+    if (n < 1 || n > (1 << 30) || m < 0 || m > int64_t(INT32_MAX) - 1) return ETL_EINVAL;
+    if (m == 0) return ETL_OK;
+    if (!edges || !is_bridge) return ETL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t A = 2 * int64_t(n - 1);  // half-edge capacity of a spanning forest
+    const int64_t N = A + 1;                // + the virtual head, at index A
+    const int64_t P = N;                    // tour positions 0 .. A
+    const int levels = sparse_levels(P);
+    Workspace ws(s);
+    int32_t *st = status ? status : ws.get<int32_t>(1);
+    int32_t *par = ws.get<int32_t>(n), *first_pos = ws.get<int32_t>(n), *end_pos = ws.get<int32_t>(n);
+    int32_t *tin = ws.get<int32_t>(n), *nlo = ws.get<int32_t>(n), *nhi = ws.get<int32_t>(n);
+    uint8_t *is_tree = ws.get<uint8_t>(m), *rflag = ws.get<uint8_t>(n);
+    int32_t *tpos = ws.get<int32_t>(m + 1), *rpos = ws.get<int32_t>(int64_t(n) + 1), *roots = ws.get<int32_t>(n);
+    int32_t *tuv = ws.get<int32_t>(A > 0 ? A : 1), *tedge = ws.get<int32_t>(n);
+    int32_t *n_arcs = ws.get<int32_t>(1), *vhead = ws.get<int32_t>(1);
+    int32_t *succ = ws.get<int32_t>(N);
+    int32_t *child = ws.get<int32_t>(n), *etin = ws.get<int32_t>(n), *etout = ws.get<int32_t>(n);
+    uint8_t *tflag = ws.get<uint8_t>(n);
+    int32_t *Lt = ws.get<int32_t>(P * levels), *Ht = ws.get<int32_t>(P * levels);
+    if (!ws.ok()) return ETL_ENOMEM;
+    etl_status rc = ETL_OK;
+    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    const int gn = grid_for(n, 256), gm = grid_for(m, 256), gA = grid_for(N, 256);
+    {
+        PhaseTimer pt("br.init", s);
+        k_init<<<gn, 256, 0, s>>>(n, par, first_pos, tin);
+        note_launch();
+    }
+    {
+        PhaseTimer pt("br.hook", s);
+        k_hook<<<gm, 256, 0, s>>>(edges, m, n, par, is_tree, st);
+        note_launch();
+    }
+    {
+        PhaseTimer pt("br.compress", s);
+        k_compress<<<gn, 256, 0, s>>>(n, par, st);
+        note_launch();
+    }
+    rc = last_launch();
+    if (!rc) rc = scan_exclusive_u8(is_tree, tpos, m, ws);
+    if (!rc) {
+        PhaseTimer pt("br.forest_edges", s);
+        k_forest_edges<<<gm, 256, 0, s>>>(edges, m, is_tree, tpos, tuv, tedge, n_arcs);
+        note_launch();
+        rc = last_launch();
+    }
+    SortResult sr{};
+    if (!rc) rc = radix_sort_pairs(tuv, nullptr, n_arcs, A > 0 ? A : 1, ceil_log2(uint64_t(n)), n, ws, &sr);
+    if (!rc) {
+        PhaseTimer pt("br.forest_succ", s);
+        k_group_bounds<<<gA, 256, 0, s>>>(sr.keys, sr.d_total, first_pos, end_pos);
+        note_launch();
+        k_forest_succ<<<gA, 256, 0, s>>>(sr.keys, sr.vals, sr.d_total, N, first_pos, end_pos, succ);
+        note_launch();
+        k_root_flags<<<gn, 256, 0, s>>>(n, par, first_pos, rflag);
+        note_launch();
+        rc = last_launch();
+    }
+    if (!rc) rc = scan_exclusive_u8(rflag, rpos, n, ws);
+    if (!rc) {
+        PhaseTimer pt("br.chain", s);
+        k_root_list<<<gn, 256, 0, s>>>(n, rflag, rpos, roots);
+        note_launch();
+        k_chain<<<gn, 256, 0, s>>>(n, rpos, roots, sr.vals, first_pos, end_pos, int32_t(A), succ);
+        note_launch();
+        rc = last_launch();
+    }
+    if (!rc) rc = set_device_i32(vhead, int32_t(A), s);
+    RankResult rr{};
+    if (!rc) rc = list_rank(succ, N, nullptr, vhead, false, -1, st, ws, &rr);
+    if (!rc) {
+        const int gt = grid_for(n, 256);
+        PhaseTimer pt("br.lowhigh_prep", s);
+        k_forest_tin<<<gt, 256, 0, s>>>(rr, n_arcs, tuv, tin, child, etin, etout);
+        note_launch();
+        k_root_tin<<<gn, 256, 0, s>>>(n, rpos, roots, sr.vals, first_pos, rr, tin);
+        note_launch();
+        k_nlo_init<<<gn, 256, 0, s>>>(n, tin, nlo, nhi);
+        note_launch();
+        k_nontree_minmax<<<gm, 256, 0, s>>>(edges, m, n, is_tree, tin, nlo, nhi);
+        note_launch();
+        k_place<<<gt, 256, 0, s>>>(n_arcs, child, etin, etout, nlo, nhi, P, Lt, Ht);
+        note_launch();
+        rc = last_launch();
+    }
+    if (!rc) rc = sparse_table_build<false>(Lt, P, levels, s);
+    if (!rc) rc = sparse_table_build<true>(Ht, P, levels, s);
+    if (!rc) {
+        PhaseTimer pt("br.test", s);
+        k_bridge_test<<<grid_for(n, 256), 256, 0, s>>>(n_arcs, etin, etout, Lt, Ht, P, tflag);
+        note_launch();
+        k_finalize<<<gm, 256, 0, s>>>(m, is_tree, tpos, tflag, st, is_bridge);
+        note_launch();
+        rc = last_launch();
+    }
+    return rc;
+}

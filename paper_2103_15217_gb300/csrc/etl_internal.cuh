@@ -1,0 +1,188 @@
+// Internal declarations of the Euler-tour library (sm_103a). Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "etl.h"
+
+#define ETL_END (-1)
+
+namespace etl {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// ----------------------------------------------------------------- host helpers
+
+// Number of SMs of the current device (cached per device).
+int num_sms();
+
+// Stream-ordered scratch: every buffer taken here is released with
+// cudaFreeAsync on the same stream when the Workspace goes out of scope.
+class Workspace {
+  public:
+    explicit Workspace(cudaStream_t s) : s_(s) {}
+    ~Workspace() { release(); }
+    Workspace(const Workspace &) = delete;
+    Workspace &operator=(const Workspace &) = delete;
+    template <class T>
+    T *get(size_t count) {
+        void *p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        if (cudaMallocAsync(&p, bytes, s_) != cudaSuccess) {
+            ok_ = false;
+            return nullptr;
+        }
+        bufs_.push_back(p);
+        return static_cast<T *>(p);
+    }
+    bool ok() const { return ok_; }
+    void release() {
+        for (void *p : bufs_) cudaFreeAsync(p, s_);
+        bufs_.clear();
+    }
+    cudaStream_t stream() const { return s_; }
+
+  private:
+    cudaStream_t s_;
+    std::vector<void *> bufs_;
+    bool ok_ = true;
+};
+
+// Brackets a launch group with CUDA events when phase timing is enabled
+// (etl_profile_enable); a no-op otherwise and while the stream is captured.
+class PhaseTimer {
+  public:
+    PhaseTimer(const char *name, cudaStream_t s);
+    ~PhaseTimer();
+    PhaseTimer(const PhaseTimer &) = delete;
+    PhaseTimer &operator=(const PhaseTimer &) = delete;
+
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    void *a_ = nullptr, *b_ = nullptr;
+};
+
+// Host-side count of kernel launches issued by the library (for reporting).
+void note_launch();
+
+inline etl_status last_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ETL_OK : ETL_ECUDA;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline int ceil_log2(uint64_t x) {  // smallest b with 2^b >= x (x >= 1)
+    int b = 0;
+    while ((uint64_t(1) << b) < x) ++b;
+    return b;
+}
+
+// ----------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ void set_status(int32_t *st, int32_t code) {
+    if (st) atomicCAS(st, 0, code);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ----------------------------------------------------------------- primitives
+
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total. If d_n is not
+// null, only in[0..*d_n) is read (the rest counts as 0); n is the capacity.
+etl_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, Workspace &ws);
+etl_status scan_exclusive_u8(const uint8_t *in, int32_t *out, int64_t n, Workspace &ws);
+
+// Stable LSD radix sort of (key, value) pairs by key, keys in [0, key_limit)
+// with key_limit <= 2^key_bits. Elements are in[0..count) where count =
+// *d_count if d_count != null else n_cap. With vals_in == null the value of
+// element i is i. Elements whose key is outside [0, key_limit) are dropped
+// (they do not appear in the output). On return
+// *keys_out / *vals_out point at the sorted arrays (inside the workspace) and
+// *d_total (device) holds the number of elements kept.
+struct SortResult {
+    const int32_t *keys;
+    const int32_t *vals;
+    const int32_t *d_total;
+};
+etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, const int32_t *d_count, int64_t n_cap,
+                            int key_bits, int32_t key_limit, Workspace &ws, SortResult *out);
+
+// ----------------------------------------------------------------- list ranking
+
+// Result of ranking one list: element e lies in sublist sid = packed[e].x at
+// local offset (packed[e].y & 0xffff) with (packed[e].y >> 16) even-indexed
+// elements before it inside the sublist; R[sid] / O[sid] are the number of
+// elements / of even-indexed elements before that sublist's first element.
+// So rank(e) = R[sid] + lr and evens_before(e) = O[sid] + lo.
+struct RankResult {
+    const uint2 *packed;
+    const int32_t *R;
+    const int32_t *O;
+    int64_t rcap;  // entries of R / O; a packed sublist id >= rcap marks an element off the list
+};
+
+struct RankParams {
+    int k0_log2 = 4;     // level-0 splitter density: one in 2^k0_log2 elements
+    int k_log2 = 4;      // density at the upper levels
+    int block = 256;     // threads per block of the walk kernels
+    int blocks_per_sm = 8;
+};
+RankParams &rank_params();
+
+// succ[0..n_cap) with elements >= *d_len (if d_len) inert; head = *d_head.
+// dual: also count even-indexed elements (the opening brackets of a tour).
+etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, const int32_t *d_head, bool dual,
+                     int64_t expect_len, int32_t *status, Workspace &ws, RankResult *out);
+
+// rank[e] for e in [0, len) (plain output of the generic list-ranking entry point)
+etl_status final_rank(const RankResult &r, int64_t len, int32_t *rank, cudaStream_t s);
+// *p = v on the stream (a kernel, so no host buffer has to outlive the call)
+etl_status set_device_i32(int32_t *p, int32_t v, cudaStream_t s);
+
+__device__ __forceinline__ int32_t rank_of(const RankResult &r, uint2 p) { return r.R[p.x] + int32_t(p.y & 0xffffu); }
+__device__ __forceinline__ int32_t evens_before(const RankResult &r, uint2 p) {
+    return r.O[p.x] + int32_t(p.y >> 16);
+}
+
+// ----------------------------------------------------------------- sparse tables
+
+// Full sparse table over x[0..n): level l holds min (or max) of x[i .. i+2^l)
+// (entries past the end are folded with the identity). levels =
+// floor(log2(max_len)) + 1 where max_len is the longest range ever queried.
+// Level 0 must already be in table[0..n).
+int sparse_levels(int64_t max_len);
+template <bool IS_MAX>
+etl_status sparse_table_build(int32_t *table, int64_t n, int levels, cudaStream_t s);
+
+template <bool IS_MAX>
+__device__ __forceinline__ int32_t sparse_query(const int32_t *__restrict__ table, int64_t n, int32_t lo,
+                                                int32_t hi) {  // inclusive range, lo <= hi
+    int len = hi - lo + 1;
+    int l = 31 - __clz(len);
+    const int32_t *t = table + int64_t(l) * n;
+    int32_t a = __ldg(t + lo), b = __ldg(t + hi - (1 << l) + 1);
+    return IS_MAX ? max(a, b) : min(a, b);
+}
+
+}  // namespace etl
+
+// ----------------------------------------------------------------- the LCA handle
+struct etl_lca_s {
+    int32_t n = 0;
+    int levels = 0;
+    cudaStream_t stream = nullptr;
+    int32_t *pre = nullptr, *depth = nullptr, *size = nullptr, *order = nullptr;
+    int32_t *table = nullptr;   // levels * n
+    int32_t *status = nullptr;  // device status word
+};

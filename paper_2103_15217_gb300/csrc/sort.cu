@@ -1,0 +1,153 @@
+// Stable LSD radix sort of (key, value) int32 pairs, 8 bits per pass.
+//
+// Used to group the arcs of a tree by their source node: children by parent
+// for a parent array, half-edges by tail for a spanning forest. This replaces
+// the lexicographic sort of array A into B in the DCEL construction of
+// Sec. 2.1: only the grouping by source is needed, and a stable sort keeps
+// each group in ascending value order.
+//
+// One pass = per-tile digit histograms -> exclusive scan over (digit, tile) ->
+// stable scatter. Inside a tile each warp ranks its 32-element rounds with
+// __match_any_sync and per-warp smem counters, so the order of equal digits is
+// preserved without any atomics on global memory.
+#include "etl_internal.cuh"
+
+namespace etl {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / kWarp;
+constexpr int kRounds = 8;                      // 32-element rounds per warp
+constexpr int kWarpTile = kWarp * kRounds;      // 256
+constexpr int kTile = kWarps * kWarpTile;       // 2048 elements per block
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ int64_t count_of(const int32_t *d_count, int64_t n_cap) {
+    if (!d_count) return n_cap;
+    int64_t c = *d_count;
+    return c < 0 ? 0 : (c < n_cap ? c : n_cap);
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_hist(const int32_t *__restrict__ keys, const int32_t *d_count, int64_t n_cap, int shift, int32_t key_limit,
+           int32_t *__restrict__ ghist, int nblocks) {
+    __shared__ int32_t h[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += kThreads) h[d] = 0;
+    __syncthreads();
+    const int64_t count = count_of(d_count, n_cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = int64_t(blockIdx.x) * kTile + warp * kWarpTile;
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        int64_t idx = base + r * kWarp + lane;
+        if (idx < count) {
+            int32_t k = keys[idx];
+            if (k >= 0 && k < key_limit) atomicAdd(&h[(k >> shift) & (kRadix - 1)], 1);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kThreads) ghist[int64_t(d) * nblocks + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, const int32_t *d_count,
+              int64_t n_cap, int shift, int32_t key_limit, const int32_t *__restrict__ goff, int nblocks,
+              int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
+    __shared__ int32_t wcnt[kWarps][kRadix];
+    __shared__ int32_t gbase[kRadix];
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t count = count_of(d_count, n_cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = int64_t(blockIdx.x) * kTile + warp * kWarpTile;
+    int32_t key[kRounds], val[kRounds], dig[kRounds], lrank[kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        int64_t idx = base + r * kWarp + lane;
+        bool valid = false;
+        int32_t k = -1;
+        if (idx < count) {
+            k = keys[idx];
+            valid = (k >= 0 && k < key_limit);
+        }
+        int d = valid ? ((k >> shift) & (kRadix - 1)) : (kRadix + lane);  // invalid lanes get unique dummies
+        unsigned peers = __match_any_sync(kFull, d);
+        int pre = 0;
+        if (valid) pre = wcnt[warp][d];
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = pre + __popc(peers);
+        __syncwarp();
+        key[r] = k;
+        val[r] = valid ? (vals ? vals[idx] : int32_t(idx)) : 0;
+        dig[r] = valid ? d : -1;
+        lrank[r] = pre + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kThreads) {
+        int32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            int32_t t = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += t;
+        }
+        gbase[d] = goff[int64_t(d) * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        if (dig[r] >= 0) {
+            int32_t dest = gbase[dig[r]] + wcnt[warp][dig[r]] + lrank[r];
+            keys_out[dest] = key[r];
+            vals_out[dest] = val[r];
+        }
+    }
+}
+
+}  // namespace
+
+etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, const int32_t *d_count, int64_t n_cap,
+                            int key_bits, int32_t key_limit, Workspace &ws, SortResult *out) {
+    cudaStream_t s = ws.stream();
+    const int64_t cap = n_cap > 0 ? n_cap : 1;
+    const int nblocks = int(ceil_div(cap, kTile));
+    const int passes = key_bits <= 8 ? 1 : (key_bits + 7) / 8;
+    if (key_bits < 31 && key_limit > (int32_t(1) << key_bits)) key_limit = int32_t(1) << key_bits;
+    int32_t *kbuf[2] = {ws.get<int32_t>(cap), ws.get<int32_t>(cap)};
+    int32_t *vbuf[2] = {ws.get<int32_t>(cap), ws.get<int32_t>(cap)};
+    int32_t *ghist = ws.get<int32_t>(int64_t(kRadix) * nblocks);
+    if (!ws.ok()) return ETL_ENOMEM;
+    const int32_t *kin = keys_in, *vin = vals_in, *cnt = d_count;
+    for (int p = 0; p < passes; ++p) {
+        int32_t *goff = ws.get<int32_t>(int64_t(kRadix) * nblocks + 1);
+        if (!ws.ok()) return ETL_ENOMEM;
+        const int shift = 8 * p;
+        etl_status st;
+        {
+            PhaseTimer pt("sort.hist", s);
+            k_hist<<<nblocks, kThreads, 0, s>>>(kin, cnt, cap, shift, key_limit, ghist, nblocks);
+        note_launch();
+            st = last_launch();
+        }
+        if (st) return st;
+        st = scan_exclusive_i32(ghist, goff, int64_t(kRadix) * nblocks, ws);
+        if (st) return st;
+        int32_t *ko = kbuf[p & 1], *vo = vbuf[p & 1];
+        {
+            PhaseTimer pt("sort.scatter", s);
+            k_scatter<<<nblocks, kThreads, 0, s>>>(kin, vin, cnt, cap, shift, key_limit, goff, nblocks, ko, vo);
+        note_launch();
+            st = last_launch();
+        }
+        if (st) return st;
+        kin = ko;
+        vin = vo;
+        cnt = goff + int64_t(kRadix) * nblocks;  // number of kept elements
+    }
+    out->keys = kin;
+    out->vals = vin;
+    out->d_total = cnt;
+    return ETL_OK;
+}
+
+}  // namespace etl
