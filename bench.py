@@ -71,6 +71,10 @@ def parse():
     ap.add_argument("--small", action="store_true", help="small sizes (functional check only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", choices=["lca", "easy", "hard"], default=None,
+                    help="run one workload of size --n twice (warm-up + one more) and exit; for profilers")
+    ap.add_argument("--n", type=int, default=1 << 22)
+    ap.add_argument("--grasp", type=int, default=0, help="tree grasp for --case lca (0 = unlimited)")
     return ap.parse_args()
 
 
@@ -440,8 +444,37 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_case(args):
+    """One workload, run twice (the second run is the one to capture)."""
+    import torch
+
+    import paper_2103_15217_gb300 as etl
+    import synth
+    etl.build()
+    dev = torch.device("cuda", 0)
+    n = args.n
+    if args.case == "lca":
+        parent = torch.from_numpy(synth.tree_parent(n, args.grasp or None, seed=1)).to(dev)
+        u, v = (torch.from_numpy(x).to(dev) for x in synth.lca_queries(n, n, seed=1))
+        for _ in range(2):
+            h = etl.lca_preprocess(parent)
+            h.query(u, v)
+            h.free()
+    else:
+        m = 8 * n if args.case == "easy" else 5 * n
+        e = synth.easy_graph(n, m, seed=1) if args.case == "easy" else synth.hard_graph(n, m - (n - 1), n // 64, seed=1)
+        edges = torch.from_numpy(e).to(dev)
+        for _ in range(2):
+            etl.find_bridges(edges, n)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "n": n, "launches": etl.launch_count()}))
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
         print(json.dumps(res))
