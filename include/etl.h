@@ -67,6 +67,28 @@ const char *etl_status_string(int32_t status);
 etl_status etl_list_rank(const int32_t *succ, int64_t len, int32_t head, int32_t *rank, int32_t *status,
                          void *stream);
 
+/*
+ * etl_list_rank_static: the same result as etl_list_rank for lists of at most
+ * 262,144 (2^18) elements, computed WITHOUT allocating any device memory.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * allocate at the point of the call -- code running under a memory manager
+ * that owns the whole device, code that must not wait on the allocator, code
+ * with a fixed memory plan. The caller still passes succ, rank and (optional)
+ * status. All scratch lives in one fixed 3 MiB __device__ array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits. Rules:
+ *  - len > 2^18 returns ETL_EINVAL and enqueues nothing;
+ *  - every call shares that array and it keeps the last call's contents (the
+ *    call clears what must start at zero); calls whose work overlaps on the
+ *    GPU (other streams, other host threads) race and produce wrong ranks, so
+ *    serialise them;
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it, so make
+ *    that first call before any stream capture on the device.
+ */
+etl_status etl_list_rank_static(const int32_t *succ, int64_t len, int32_t head, int32_t *rank, int32_t *status,
+                                void *stream);
+
 /* ------------------------------------------------------------------ LCA
  * Lowest common ancestors (Sec. 3): preprocessing builds the Euler tour of the
  * tree (Sec. 2.1, successor = next(twin)), ranks it once (Sec. 2.2), derives

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libetl.so")
 
 STATUS = {0: "ETL_OK", 1: "ETL_EINVAL", 2: "ETL_ENOMEM", 3: "ETL_ECUDA", 4: "ETL_EBADTREE",
           5: "ETL_EBADQUERY", 6: "ETL_EBADGRAPH", 7: "ETL_ETIMEOUT"}
-EXPORTS = ("etl_status_string", "etl_list_rank", "lca_preprocess", "lca_query", "lca_status", "lca_arrays",
+EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_preprocess", "lca_query", "lca_status", "lca_arrays",
            "lca_export", "lca_free", "find_bridges", "etl_profile_enable", "etl_profile_reset",
            "etl_profile_count", "etl_profile_get", "etl_launch_count")
 
@@ -60,6 +60,7 @@ def load_library(path: str | None = None):
         lib.etl_status_string.argtypes = [i32]
         lib.etl_status_string.restype = ctypes.c_char_p
         lib.etl_list_rank.argtypes = [P, i64, i32, P, P, P]
+        lib.etl_list_rank_static.argtypes = [P, i64, i32, P, P, P]
         lib.lca_preprocess.argtypes = [P, i32, P, PP]
         lib.lca_query.argtypes = [P, P, P, i64, P, P, P]
         lib.lca_status.argtypes = [P, ctypes.POINTER(i32)]

@@ -26,6 +26,7 @@
 // preorder number, so preorder comes straight out of the ranking without a
 // scatter + scan over the tour.
 #include <cstdio>
+#include <mutex>
 
 #include "etl_internal.cuh"
 
@@ -466,3 +467,160 @@ etl_status final_rank(const RankResult &r, int64_t len, int32_t *rank, cudaStrea
 }
 
 }  // namespace etl
+
+// ------------------------------------------------------------------ list ranking without allocation
+//
+// etl_list_rank_static: the same ranking as etl_list_rank, but every byte of
+// scratch it needs comes from one fixed array of device memory that the
+// library reserves when it is loaded, so the call itself never allocates.
+// It exists for callers that cannot allocate device memory at the point of
+// the call: code that runs under an external memory manager that owns the
+// whole device (so a cudaMalloc would fail or fragment its arena), code that
+// must not block on the allocator's implicit synchronisation, and code with a
+// fixed, pre-planned memory budget. Such callers still pass their own input
+// and output arrays.
+//
+// Limits and rules (also in etl.h):
+//  * len <= kStaticMaxLen (2^18 elements); larger lists are rejected with
+//    ETL_EINVAL before anything is enqueued.
+//  * The scratch array (kStaticBytes, 3 MiB) is a file-scope __device__
+//    variable: every GPU on which the library is loaded holds it until the
+//    process exits.
+//  * All calls share it and it keeps the previous call's contents; the
+//    counters that must start at zero are cleared by each call. Two calls
+//    whose work overlaps on the GPU (different streams, or different host
+//    threads) race on the same scratch and give wrong ranks: serialise them.
+//  * The host cannot use the array's name as a device address, so the first
+//    call on each device looks the address up with cudaGetSymbolAddress (with
+//    that device current) and caches it; that first call should therefore
+//    come before any stream capture on that device.
+namespace etl {
+namespace {
+
+constexpr int64_t kStaticMaxLen = int64_t(1) << 18;
+constexpr size_t kStaticBytes = size_t(3) << 20;
+constexpr int kStaticK0 = 4, kStaticK = 4;  // fixed splitter densities, so the layout is fixed
+
+static __device__ __align__(256) unsigned char g_rank_scratch[kStaticBytes];
+
+struct StaticArena {
+    char *base;
+    size_t used, cap;
+    template <class T>
+    T *take(int64_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        size_t bytes = size_t(count > 0 ? count : 1) * sizeof(T);
+        if (off + bytes > cap) return nullptr;
+        used = off + bytes;
+        return reinterpret_cast<T *>(base + off);
+    }
+};
+
+std::mutex g_static_mu;
+void *g_static_addr[64] = {nullptr};
+
+// once per device, with that device current: the device address of the scratch array
+etl_status static_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ETL_ECUDA;
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_rank_scratch) != cudaSuccess || !p) return ETL_ECUDA;
+        if (cudaFuncSetAttribute(k_pointer_jump, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kPjCap * 4) !=
+            cudaSuccess)
+            return ETL_ECUDA;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return ETL_OK;
+}
+
+}  // namespace
+}  // namespace etl
+
+extern "C" etl_status etl_list_rank_static(const int32_t *succ, int64_t len, int32_t head, int32_t *rank,
+                                           int32_t *status, void *stream) {
+    using namespace etl;
+    if (!succ || !rank || len < 1 || head < 0 || head >= len) return ETL_EINVAL;
+    if (len > kStaticMaxLen) return ETL_EINVAL;  // beyond the fixed scratch: documented limit
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    etl_status rc = static_scratch(&scratch);
+    if (rc) return rc;
+    StaticArena A{static_cast<char *>(scratch), 0, kStaticBytes};
+    const int grid = num_sms() * 8;
+    const int block = 256;
+
+    int32_t *word = A.take<int32_t>(4);  // [0] head, [1] status when the caller passes none
+    int32_t *st = status ? status : word + 1;
+    Hash H = make_hash(len, kStaticK0);
+    const int32_t dyn_cap = int32_t(len / kLcap + 2);
+    const int64_t cap1 = int64_t(H.S0) + 1 + dyn_cap;
+    uint2 *packed = A.take<uint2>(len);
+    int32_t *rnext = A.take<int32_t>(cap1), *rw1 = A.take<int32_t>(cap1), *rw2 = A.take<int32_t>(cap1);
+    int32_t *ctr = A.take<int32_t>(2), *head1 = A.take<int32_t>(1);
+    if (!word || !packed || !rnext || !rw1 || !rw2 || !ctr || !head1) return ETL_ENOMEM;
+
+    if (!status && cudaMemsetAsync(st, 0, sizeof(int32_t), s) != cudaSuccess) return ETL_ECUDA;
+    if (cudaMemsetAsync(ctr, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return ETL_ECUDA;
+    k_set_i32<<<1, 1, 0, s>>>(word, head);
+    note_launch();
+    k_walk0<false><<<grid, block, 0, s>>>(succ, len, word, H, packed, rnext, rw1, rw2, ctr, dyn_cap, head1, st);
+    note_launch();
+    if ((rc = last_launch())) return rc;
+
+    struct Level {
+        const int32_t *succ, *w1, *w2;
+        int64_t base, cap;
+        const int32_t *d_add, *d_head;
+        int4 *loc;
+        int32_t *R, *O;
+    };
+    Level lv[8];
+    int nl = 0;
+    lv[nl++] = Level{rnext, rw1, rw2, int64_t(H.S0) + 1, cap1, ctr + 1, head1, nullptr, nullptr, nullptr};
+    while (lv[nl - 1].cap > kPjCap) {
+        if (nl >= 8) return ETL_ENOMEM;
+        Level &L = lv[nl - 1];
+        Hash h = make_hash(L.cap, kStaticK);
+        const int32_t dcap = int32_t(L.cap / kLcap + 2);
+        const int64_t ncap = int64_t(h.S0) + 1 + dcap;
+        L.loc = A.take<int4>(L.cap);
+        int32_t *nn = A.take<int32_t>(ncap), *n1 = A.take<int32_t>(ncap), *n2 = A.take<int32_t>(ncap);
+        int32_t *c = A.take<int32_t>(2), *hd = A.take<int32_t>(1);
+        if (!L.loc || !nn || !n1 || !n2 || !c || !hd) return ETL_ENOMEM;
+        if (cudaMemsetAsync(c, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return ETL_ECUDA;
+        if (cudaMemsetAsync(L.loc, 0xff, size_t(L.cap) * sizeof(int4), s) != cudaSuccess) return ETL_ECUDA;
+        k_walk<<<grid, block, 0, s>>>(L.succ, L.w1, L.w2, L.base, L.d_add, L.cap, L.d_head, h, L.loc, nn, n1, n2, c,
+                                      dcap, hd, st);
+        note_launch();
+        if ((rc = last_launch())) return rc;
+        lv[nl++] = Level{nn, n1, n2, int64_t(h.S0) + 1, ncap, c + 1, hd, nullptr, nullptr, nullptr};
+    }
+    Level &T = lv[nl - 1];
+    T.R = A.take<int32_t>(T.cap);
+    T.O = A.take<int32_t>(T.cap);
+    if (!T.R || !T.O) return ETL_ENOMEM;
+    k_pointer_jump<<<1, kPjThreads, 4 * kPjCap * 4, s>>>(T.succ, T.w1, T.w2, T.base, T.d_add, T.cap, T.d_head, len,
+                                                          T.R, T.O, st);
+    note_launch();
+    if ((rc = last_launch())) return rc;
+    for (int i = nl - 2; i >= 0; --i) {
+        Level &L = lv[i];
+        L.R = A.take<int32_t>(L.cap);
+        L.O = A.take<int32_t>(L.cap);
+        if (!L.R || !L.O) return ETL_ENOMEM;
+        int blocks = int(ceil_div(L.cap, 256));
+        if (blocks > grid * 4) blocks = grid * 4;
+        k_expand<<<blocks, 256, 0, s>>>(L.loc, L.base, L.d_add, L.cap, lv[i + 1].cap, lv[i + 1].R, lv[i + 1].O, L.R,
+                                        L.O);
+        note_launch();
+        if ((rc = last_launch())) return rc;
+    }
+    int blocks = int(ceil_div(len, 256));
+    if (blocks > num_sms() * 16) blocks = num_sms() * 16;
+    k_final_rank<<<blocks, 256, 0, s>>>(packed, len, lv[0].R, lv[0].cap, rank);
+    note_launch();
+    return last_launch();
+}
