@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="small sizes (functional check only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", choices=["all", "core", "batched"], default="all",
+                    help="core = the scale workload; batched = 4096 mixed instances, batched vs per-instance")
     ap.add_argument("--case", choices=["lca", "easy", "hard"], default=None,
                     help="run one workload of size --n twice (warm-up + one more) and exit; for profilers")
     ap.add_argument("--n", type=int, default=1 << 22)
@@ -284,6 +286,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, etl, trees, graphs, dev, units, world)
 
+    if args.mode in ("all", "batched"):
+        batched_res = run_batched(args, dev)
+    else:
+        batched_res = None
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -294,6 +300,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "wall_s_timed": wall},
         "breakdown": breakdown,
+        "batched": batched_res,
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,
@@ -383,6 +390,114 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
     t = a.elapsed_time(b) / 1e3 / args.steps
     return {"value": units * world / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": t * 1e3}
+
+
+# ------------------------------------------------------------------ batched instances
+
+def make_batch_inputs(small: bool, seed: int = 1):
+    import synth
+    from synth.generators import make_graph, make_tree
+    nt, ng = (64, 64) if small else (2048, 2048)
+    trees, graphs = synth.batched_instances(seed=seed, ntrees=nt, ngraphs=ng)
+    tp, tu, tv, ti, toff = [], [], [], [], [0]
+    for i, d in enumerate(trees):
+        p, u, v = make_tree(d)
+        tp.append(p)
+        tu.append(u)
+        tv.append(v)
+        ti.append(np.full(u.shape[0], i, np.int32))
+        toff.append(toff[-1] + d["n"])
+    ge, eoff, noff = [], [0], [0]
+    for d in graphs:
+        e = make_graph(d)
+        ge.append(e)
+        eoff.append(eoff[-1] + e.shape[0])
+        noff.append(noff[-1] + d["n"])
+    return dict(trees=trees, graphs=graphs, tp=tp, tu=tu, tv=tv, ti=ti, toff=np.array(toff, np.int32),
+                ge=ge, eoff=np.array(eoff, np.int32), noff=np.array(noff, np.int32))
+
+
+def run_batched(args, dev):
+    """Per-instance launches vs one batched, graph-captured launch sequence (equal results required)."""
+    import torch
+
+    import paper_2103_15217_gb300 as etl
+    B = make_batch_inputs(args.small)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    tp = [T(x) for x in B["tp"]]
+    tu = [T(x) for x in B["tu"]]
+    tv = [T(x) for x in B["tv"]]
+    ge = [T(x) for x in B["ge"]]
+    P, O = T(np.concatenate(B["tp"])), T(B["toff"])
+    I, U, V = T(np.concatenate(B["ti"])), T(np.concatenate(B["tu"])), T(np.concatenate(B["tv"]))
+    E, EO, NO = T(np.concatenate(B["ge"])), T(B["eoff"]), T(B["noff"])
+    max_n = max(d["n"] for d in B["trees"])
+    total_gn = int(B["noff"][-1])
+    q_total, m_total = int(U.numel()), int(E.shape[0])
+    units = q_total + m_total
+    outs_pi = [torch.empty_like(u) for u in tu]
+    masks_pi = [torch.empty(e.shape[0], dtype=torch.uint8, device=dev) for e in ge]
+    out_b = torch.empty_like(U)
+    mask_b = torch.empty(m_total, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def per_instance():
+        for i in range(len(tp)):
+            h = etl.lca_preprocess(tp[i])
+            h.query(tu[i], tv[i], out=outs_pi[i])
+            h.free()
+        for i, d in enumerate(B["graphs"]):
+            masks_pi[i].copy_(etl.find_bridges(ge[i], d["n"]))
+
+    def batched():
+        h = etl.lca_preprocess_batch(P, O, max_n)
+        h.query_batch(I, U, V, out=out_b)
+        h.free()
+        mask_b.copy_(etl.find_bridges_batch(E, EO, NO, total_gn))
+
+    def timed(fn, reps, graph=None):
+        ts = []
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                graph.replay() if graph is not None else fn()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b) / 1e3)
+        return statistics.mean(ts)
+
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        per_instance()
+        batched()
+    torch.cuda.synchronize()
+    equal = bool(torch.equal(torch.cat(outs_pi), out_b) and torch.equal(torch.cat(masks_pi), mask_b))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batched()
+    steps = max(1, min(args.steps, 3))
+    t_pi = timed(per_instance, steps)
+    for _ in range(max(1, args.warmup)):
+        g.replay()
+    torch.cuda.synchronize()
+    l0 = etl.launch_count()
+    t_b = timed(None, args.steps, graph=g)
+    launches_b = etl.launch_count() - l0  # graph replays do not go through the library's launch sites
+    g.replay()
+    torch.cuda.synchronize()
+    equal = equal and bool(torch.equal(torch.cat(outs_pi), out_b) and torch.equal(torch.cat(masks_pi), mask_b))
+    return {
+        "workload": (f"{len(tp)} trees n log-uniform 2^6..2^18 (grasp 1, 1024, inf round robin) with n queries each"
+                     f" + {len(ge)} graphs n log-uniform 2^6..2^16, m = 4n (easy/hard alternating)"),
+        "queries": q_total, "edges": m_total, "tree_nodes": int(B["toff"][-1]), "graph_nodes": total_gn,
+        "per_instance": {"ms": t_pi * 1e3, "value": units / t_pi},
+        "batched_graph": {"ms": t_b * 1e3, "value": units / t_b, "captured": True},
+        "speedup": t_pi / t_b, "results_identical": equal, "unit": UNIT,
+        "host_launch_sites_during_replay": launches_b,
+    }
 
 
 # ------------------------------------------------------------------ CPU oracle arm

@@ -124,6 +124,35 @@ etl_status lca_query(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q,
                      int32_t *status, void *stream);
 
 /*
+ * lca_preprocess_batch: k independent trees preprocessed together (one
+ * launch sequence for all of them). parent[0..total_n) is the concatenation of
+ * the trees' parent arrays in LOCAL ids: tree i owns entries node_off[i] ..
+ * node_off[i+1]-1, its nodes are numbered 0 .. size-1 and its root has -1.
+ * node_off is a DEVICE int32[k+1] array with node_off[0] = 0, node_off[k] =
+ * total_n and every tree non-empty (else ETL_EINVAL in the status word).
+ * max_n (host) must be >= the largest tree's size; it sizes the sparse table.
+ * The trees' Euler tours are chained into one list and ranked once; tree i
+ * then occupies preorder positions node_off[i] .. node_off[i+1]-1, so
+ * lca_arrays / lca_export return GLOBAL preorder numbers (pre - node_off[i]
+ * is the preorder inside tree i; depth and size are per tree). k >= 1,
+ * total_n in [k, 2^30].
+ */
+etl_status lca_preprocess_batch(const int32_t *parent, const int32_t *node_off, int32_t k, int32_t total_n,
+                                int32_t max_n, void *stream, etl_lca_t *out);
+
+/*
+ * lca_query_batch: for a handle from lca_preprocess_batch, out[i] =
+ * LCA(u[i], v[i]) in tree inst[i], with u, v and the answer in that tree's
+ * LOCAL ids. inst, u, v, out are device int32[q]; queries of different trees
+ * may be mixed in any order. A tree index outside [0, k) or an id outside the
+ * tree gives -1 and ETL_EBADQUERY in *status (device, may be NULL, never
+ * cleared). lca_query on a batch handle (and this call on a single-tree
+ * handle) returns ETL_EINVAL.
+ */
+etl_status lca_query_batch(etl_lca_t h, const int32_t *inst, const int32_t *u, const int32_t *v, int64_t q,
+                           int32_t *out, int32_t *status, void *stream);
+
+/*
  * lca_status: waits for the stream the handle was built on, then writes the
  * handle's data status (an etl_status code, 0 = the tree was valid) to the
  * HOST int32 *status. Synchronising.
@@ -168,6 +197,34 @@ etl_status lca_free(etl_lca_t h);
 etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
                         void *stream);
 
+/* ------------------------------------------------------------------ tuning knobs
+ * Launch parameters that do not change any result, exposed for the autotuner
+ * (paper_2103_15217_gb300/tune.py). Process-wide; set them between calls,
+ * not while calls are being enqueued from another thread.
+ *   ETL_TUNE_RANK_K0_LOG2   level-0 splitter density of the list ranker: one
+ *                           splitter per 2^k elements, k in [1, 8] (default 4)
+ *   ETL_TUNE_RANK_K_LOG2    density at the upper ranking levels, [1, 8] (4)
+ *   ETL_TUNE_RANK_BLOCK     threads per block of the walk kernels, one of
+ *                           64, 128, 256, 512, 1024 (256)
+ *   ETL_TUNE_RANK_BLOCKS_PER_SM  resident walk blocks per SM, block * value
+ *                           <= 2048 (8)
+ *   ETL_TUNE_RMQ_LEVELS_PER_PASS sparse-table levels built per streaming
+ *                           pass, 1..3 (3)
+ *   ETL_TUNE_RMQ_BLOCK      threads per block of the sparse-table build,
+ *                           128, 256, 512 or 1024 (256)
+ * Unknown keys or out-of-range values return ETL_EINVAL.
+ */
+enum {
+    ETL_TUNE_RANK_K0_LOG2 = 1,
+    ETL_TUNE_RANK_K_LOG2 = 2,
+    ETL_TUNE_RANK_BLOCK = 3,
+    ETL_TUNE_RANK_BLOCKS_PER_SM = 4,
+    ETL_TUNE_RMQ_LEVELS_PER_PASS = 5,
+    ETL_TUNE_RMQ_BLOCK = 6
+};
+etl_status etl_tune_set(int32_t key, int32_t value);
+etl_status etl_tune_get(int32_t key, int32_t *value);
+
 /* ------------------------------------------------------------------ phase timers
  * Opt-in device timing of the library's own launch groups (not part of the
  * method; used by the benchmark). When enabled, each launch group is
@@ -182,6 +239,20 @@ etl_status etl_profile_count(int32_t *count);
 etl_status etl_profile_get(int32_t i, char *name, int32_t name_len, double *total_ms, int64_t *launches);
 /* Number of kernels this process has launched through the library so far (host-side counter). */
 etl_status etl_launch_count(int64_t *count);
+
+/*
+ * find_bridges_batch: k independent graphs in one launch sequence.
+ * edges[0..2*total_m) is the concatenation of the graphs' edge lists in LOCAL
+ * node ids; graph i owns edges edge_off[i] .. edge_off[i+1]-1 and nodes
+ * 0 .. node_off[i+1]-node_off[i]-1. edge_off and node_off are DEVICE
+ * int32[k+1] arrays, non-decreasing from 0 to total_m / total_n, every graph
+ * with at least one node (else ETL_EINVAL in the status word). Writes
+ * is_bridge[e] for every edge of every graph, the same as find_bridges on
+ * that graph alone. The disjoint union is processed as one graph: bridges of
+ * a disjoint union are the bridges of its parts.
+ */
+etl_status find_bridges_batch(const int32_t *edges, const int32_t *edge_off, const int32_t *node_off, int32_t k,
+                              int64_t total_m, int32_t total_n, uint8_t *is_bridge, int32_t *status, void *stream);
 
 #ifdef __cplusplus
 }

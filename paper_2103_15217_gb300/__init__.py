@@ -26,8 +26,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libetl.so")
 STATUS = {0: "ETL_OK", 1: "ETL_EINVAL", 2: "ETL_ENOMEM", 3: "ETL_ECUDA", 4: "ETL_EBADTREE",
           5: "ETL_EBADQUERY", 6: "ETL_EBADGRAPH", 7: "ETL_ETIMEOUT"}
 EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_preprocess", "lca_query", "lca_status", "lca_arrays",
-           "lca_export", "lca_free", "find_bridges", "etl_profile_enable", "etl_profile_reset",
-           "etl_profile_count", "etl_profile_get", "etl_launch_count")
+           "lca_export", "lca_free", "find_bridges", "lca_preprocess_batch", "lca_query_batch", "find_bridges_batch", "etl_profile_enable", "etl_profile_reset",
+           "etl_profile_count", "etl_profile_get", "etl_launch_count", "etl_tune_set", "etl_tune_get")
+TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
+             "rmq_levels_per_pass": 5, "rmq_block": 6}
 
 _lock = threading.Lock()
 _lib = None
@@ -68,7 +70,12 @@ def load_library(path: str | None = None):
         lib.lca_export.argtypes = [P, P, P, P, P, P]
         lib.lca_free.argtypes = [P]
         lib.find_bridges.argtypes = [P, i64, i32, P, P, P]
+        lib.lca_preprocess_batch.argtypes = [P, P, i32, i32, i32, P, PP]
+        lib.lca_query_batch.argtypes = [P, P, P, P, i64, P, P, P]
+        lib.find_bridges_batch.argtypes = [P, P, P, i32, i64, i32, P, P, P]
         lib.etl_launch_count.argtypes = [ctypes.POINTER(i64)]
+        lib.etl_tune_set.argtypes = [i32, i32]
+        lib.etl_tune_get.argtypes = [i32, ctypes.POINTER(i32)]
         lib.etl_profile_enable.argtypes = [i32]
         lib.etl_profile_reset.argtypes = []
         lib.etl_profile_count.argtypes = [ctypes.POINTER(i32)]
@@ -118,17 +125,26 @@ def list_rank(succ: torch.Tensor, head: int, status: torch.Tensor | None = None,
 
 
 class Lca:
-    """A preprocessed tree: wraps an ``etl_lca_t`` handle."""
+    """A preprocessed tree, or a batch of trees: wraps an ``etl_lca_t`` handle."""
 
-    def __init__(self, parent: torch.Tensor, stream=None):
+    def __init__(self, parent: torch.Tensor, stream=None, node_off: torch.Tensor | None = None,
+                 max_n: int | None = None):
         lib = load_library()
         self._lib = lib
         self.n = parent.numel()
+        self.batched = node_off is not None
         self._h = ctypes.c_void_p()
         self._stream = _stream(stream)
-        _check("lca_preprocess", lib.lca_preprocess(_dev_i32(parent, "parent"), self.n, self._stream,
-                                                    ctypes.byref(self._h)))
-        self._parent_ref = parent  # keep the input alive until preprocessing has run
+        if self.batched:
+            self.k = node_off.numel() - 1
+            _check("lca_preprocess_batch", lib.lca_preprocess_batch(
+                _dev_i32(parent, "parent"), _dev_i32(node_off, "node_off"), self.k, self.n,
+                int(max_n if max_n is not None else self.n), self._stream, ctypes.byref(self._h)))
+        else:
+            self.k = 1
+            _check("lca_preprocess", lib.lca_preprocess(_dev_i32(parent, "parent"), self.n, self._stream,
+                                                        ctypes.byref(self._h)))
+        self._refs = (parent, node_off)  # keep the inputs alive until preprocessing has run
 
     def query(self, u: torch.Tensor, v: torch.Tensor, out: torch.Tensor | None = None,
               status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -138,6 +154,18 @@ class Lca:
             out = torch.empty_like(u)
         _check("lca_query", self._lib.lca_query(self._h, _dev_i32(u, "u"), _dev_i32(v, "v"), u.numel(),
                                                 _dev_i32(out, "out"), _status_ptr(status), _stream(stream)))
+        return out
+
+    def query_batch(self, inst: torch.Tensor, u: torch.Tensor, v: torch.Tensor, out: torch.Tensor | None = None,
+                    status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Queries of a batch handle: tree ``inst[i]``, local ids in and out."""
+        if not (u.numel() == v.numel() == inst.numel()):
+            raise ValueError("inst, u and v must have the same length")
+        if out is None:
+            out = torch.empty_like(u)
+        _check("lca_query_batch", self._lib.lca_query_batch(self._h, _dev_i32(inst, "inst"), _dev_i32(u, "u"),
+                                                            _dev_i32(v, "v"), u.numel(), _dev_i32(out, "out"),
+                                                            _status_ptr(status), _stream(stream)))
         return out
 
     def status(self) -> int:
@@ -171,6 +199,23 @@ def profile_enable(on: bool = True):
     _check("etl_profile_enable", load_library().etl_profile_enable(1 if on else 0))
 
 
+def tune_set(**params):
+    """Set launch parameters (no effect on results): rank_k0_log2, rank_k_log2, rank_block, rank_blocks_per_sm."""
+    lib = load_library()
+    for k, v in params.items():
+        _check(f"etl_tune_set({k})", lib.etl_tune_set(TUNE_KEYS[k], int(v)))
+
+
+def tune_get() -> dict:
+    lib = load_library()
+    out = {}
+    for k, key in TUNE_KEYS.items():
+        v = ctypes.c_int32(0)
+        _check("etl_tune_get", lib.etl_tune_get(key, ctypes.byref(v)))
+        out[k] = v.value
+    return out
+
+
 def launch_count() -> int:
     """Kernels launched by the library in this process so far."""
     c = ctypes.c_int64(0)
@@ -198,6 +243,27 @@ def profile_read() -> dict:
 
 def lca_preprocess(parent: torch.Tensor, stream=None) -> Lca:
     return Lca(parent, stream)
+
+
+def lca_preprocess_batch(parent: torch.Tensor, node_off: torch.Tensor, max_n: int, stream=None) -> Lca:
+    """Trees concatenated in local ids; node_off (device int32[k+1]) delimits them."""
+    return Lca(parent, stream, node_off=node_off, max_n=max_n)
+
+
+def find_bridges_batch(edges: torch.Tensor, edge_off: torch.Tensor, node_off: torch.Tensor, total_n: int,
+                       status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Bridge masks of k graphs concatenated in local ids (edge_off / node_off: device int32[k+1],
+    total_n = node_off[k] given by the caller so that nothing is read back from the device)."""
+    lib = load_library()
+    if edges.dim() != 2 or edges.shape[1] != 2:
+        raise ValueError("edges must have shape (m, 2)")
+    k = node_off.numel() - 1
+    m = edges.shape[0]
+    mask = torch.empty(m, dtype=torch.uint8, device=edges.device)
+    _check("find_bridges_batch", lib.find_bridges_batch(_dev_i32(edges, "edges"), _dev_i32(edge_off, "edge_off"),
+                                                        _dev_i32(node_off, "node_off"), k, m, total_n,
+                                                        mask.data_ptr(), _status_ptr(status), _stream(stream)))
+    return mask
 
 
 def find_bridges(edges: torch.Tensor, n: int, status: torch.Tensor | None = None, stream=None) -> torch.Tensor:

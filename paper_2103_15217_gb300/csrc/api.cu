@@ -52,3 +52,50 @@ extern "C" etl_status etl_list_rank(const int32_t *succ, int64_t len, int32_t he
     if (!rc) rc = final_rank(rr, len, rank, s);
     return rc;
 }
+
+extern "C" etl_status etl_tune_set(int32_t key, int32_t value) {
+    RankParams &P = rank_params();
+    switch (key) {
+        case ETL_TUNE_RANK_K0_LOG2:
+            if (value < 1 || value > 8) return ETL_EINVAL;
+            P.k0_log2 = value;
+            return ETL_OK;
+        case ETL_TUNE_RANK_K_LOG2:
+            if (value < 1 || value > 8) return ETL_EINVAL;
+            P.k_log2 = value;
+            return ETL_OK;
+        case ETL_TUNE_RANK_BLOCK:
+            if (value != 64 && value != 128 && value != 256 && value != 512 && value != 1024) return ETL_EINVAL;
+            if (value * P.blocks_per_sm > 2048) P.blocks_per_sm = 2048 / value;
+            P.block = value;
+            return ETL_OK;
+        case ETL_TUNE_RANK_BLOCKS_PER_SM:
+            if (value < 1 || value * P.block > 2048) return ETL_EINVAL;
+            P.blocks_per_sm = value;
+            return ETL_OK;
+        case ETL_TUNE_RMQ_LEVELS_PER_PASS:
+            if (value < 1 || value > 3) return ETL_EINVAL;
+            rmq_params().levels_per_pass = value;
+            return ETL_OK;
+        case ETL_TUNE_RMQ_BLOCK:
+            if (value != 128 && value != 256 && value != 512 && value != 1024) return ETL_EINVAL;
+            rmq_params().block = value;
+            return ETL_OK;
+        default:
+            return ETL_EINVAL;
+    }
+}
+
+extern "C" etl_status etl_tune_get(int32_t key, int32_t *value) {
+    if (!value) return ETL_EINVAL;
+    const RankParams &P = rank_params();
+    switch (key) {
+        case ETL_TUNE_RANK_K0_LOG2: *value = P.k0_log2; return ETL_OK;
+        case ETL_TUNE_RANK_K_LOG2: *value = P.k_log2; return ETL_OK;
+        case ETL_TUNE_RANK_BLOCK: *value = P.block; return ETL_OK;
+        case ETL_TUNE_RANK_BLOCKS_PER_SM: *value = P.blocks_per_sm; return ETL_OK;
+        case ETL_TUNE_RMQ_LEVELS_PER_PASS: *value = rmq_params().levels_per_pass; return ETL_OK;
+        case ETL_TUNE_RMQ_BLOCK: *value = rmq_params().block; return ETL_OK;
+        default: return ETL_EINVAL;
+    }
+}

@@ -246,7 +246,7 @@ __global__ void k_place(const int32_t *__restrict__ d_arcs, const int32_t *__res
 
 __global__ void k_bridge_test(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ etin,
                               const int32_t *__restrict__ etout, const int32_t *__restrict__ Lt,
-                              const int32_t *__restrict__ Ht, int64_t P, uint8_t *__restrict__ tflag) {
+                              const int32_t *__restrict__ Ht, int64_t P, int64_t ld, uint8_t *__restrict__ tflag) {
     const int64_t T = *d_arcs / 2;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
         const int32_t a = etin[t], b = etout[t];
@@ -254,8 +254,8 @@ __global__ void k_bridge_test(const int32_t *__restrict__ d_arcs, const int32_t 
             tflag[t] = 0;
             continue;
         }
-        const int32_t low = sparse_query<false>(Lt, P, a, b);
-        const int32_t high = sparse_query<true>(Ht, P, a, b);
+        const int32_t low = sparse_query<false>(Lt, ld, a, b);
+        const int32_t high = sparse_query<true>(Ht, ld, a, b);
         tflag[t] = (low >= a && high <= b) ? 1 : 0;
     }
 }
@@ -278,20 +278,18 @@ int grid_for(int64_t work, int threads) {
 }  // namespace
 }  // namespace etl
 
-using namespace etl;
+namespace etl {
+namespace {
 
-extern "C" etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
-                                   void *stream) {
-    if (n < 1 || n > (1 << 30) || m < 0 || m > int64_t(INT32_MAX) - 1) return ETL_EINVAL;
-    if (m == 0) return ETL_OK;
-    if (!edges || !is_bridge) return ETL_EINVAL;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+// the whole Tarjan-Vishkin pipeline on a graph with global ids; st is a zeroed device status word
+etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *st,
+                        Workspace &ws) {
+    cudaStream_t s = ws.stream();
     const int64_t A = 2 * int64_t(n - 1);  // half-edge capacity of a spanning forest
     const int64_t N = A + 1;                // + the virtual head, at index A
     const int64_t P = N;                    // tour positions 0 .. A
     const int levels = sparse_levels(P);
-    Workspace ws(s);
-    int32_t *st = status ? status : ws.get<int32_t>(1);
+    const int64_t ld = sparse_ld(P);
     int32_t *par = ws.get<int32_t>(n), *first_pos = ws.get<int32_t>(n), *end_pos = ws.get<int32_t>(n);
     int32_t *tin = ws.get<int32_t>(n), *nlo = ws.get<int32_t>(n), *nhi = ws.get<int32_t>(n);
     uint8_t *is_tree = ws.get<uint8_t>(m), *rflag = ws.get<uint8_t>(n);
@@ -301,10 +299,9 @@ extern "C" etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, u
     int32_t *succ = ws.get<int32_t>(N);
     int32_t *child = ws.get<int32_t>(n), *etin = ws.get<int32_t>(n), *etout = ws.get<int32_t>(n);
     uint8_t *tflag = ws.get<uint8_t>(n);
-    int32_t *Lt = ws.get<int32_t>(P * levels), *Ht = ws.get<int32_t>(P * levels);
+    int32_t *Lt = ws.get<int32_t>(ld * levels), *Ht = ws.get<int32_t>(ld * levels);
     if (!ws.ok()) return ETL_ENOMEM;
     etl_status rc = ETL_OK;
-    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
     const int gn = grid_for(n, 256), gm = grid_for(m, 256), gA = grid_for(N, 256);
     {
         PhaseTimer pt("br.init", s);
@@ -372,11 +369,99 @@ extern "C" etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, u
     if (!rc) rc = sparse_table_build<true>(Ht, P, levels, s);
     if (!rc) {
         PhaseTimer pt("br.test", s);
-        k_bridge_test<<<grid_for(n, 256), 256, 0, s>>>(n_arcs, etin, etout, Lt, Ht, P, tflag);
+        k_bridge_test<<<grid_for(n, 256), 256, 0, s>>>(n_arcs, etin, etout, Lt, Ht, P, ld, tflag);
         note_launch();
         k_finalize<<<gm, 256, 0, s>>>(m, is_tree, tpos, tflag, st, is_bridge);
         note_launch();
         rc = last_launch();
     }
     return rc;
+}
+
+// local edge ids of a batch -> global ids: edge e of instance i (edge_off[i] <= e < edge_off[i+1])
+// joins node_off[i] + u and node_off[i] + v
+__global__ void k_check_batch(const int32_t *__restrict__ eoff, const int32_t *__restrict__ noff, int32_t k,
+                              int64_t m, int32_t n, int32_t *__restrict__ bad, int32_t *__restrict__ status) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < k; i += int64_t(gridDim.x) * blockDim.x) {
+        const bool ok = eoff[i] >= 0 && eoff[i] <= eoff[i + 1] && eoff[i + 1] <= m && noff[i] >= 0 &&
+                        noff[i] < noff[i + 1] && noff[i + 1] <= n && (i > 0 || (eoff[0] == 0 && noff[0] == 0)) &&
+                        (i < k - 1 || (eoff[k] == m && noff[k] == n));
+        if (!ok) {
+            set_status(status, ETL_EINVAL);
+            *bad = 1;
+        }
+    }
+}
+
+__global__ void k_globalize(const int32_t *__restrict__ edges, int64_t m, const int32_t *__restrict__ eoff,
+                            const int32_t *__restrict__ noff, int32_t k, const int32_t *__restrict__ bad,
+                            int32_t *__restrict__ gedges, int32_t *__restrict__ status) {
+    const bool unusable = *bad != 0;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        int32_t gu = -1, gv = -1;
+        if (!unusable) {
+            int32_t lo = 0, hi = k;  // largest i with eoff[i] <= e (offsets checked monotone above)
+            while (lo < hi) {
+                const int32_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(eoff + mid) <= e) lo = mid; else hi = mid - 1;
+            }
+            if (lo < k) {
+                const int32_t base = __ldg(noff + lo), size = __ldg(noff + lo + 1) - base;
+                const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+                if (a >= 0 && a < size && b >= 0 && b < size) {
+                    gu = a + base;
+                    gv = b + base;
+                }
+            }
+            if (gu < 0) set_status(status, ETL_EBADGRAPH);
+        }
+        gedges[2 * e] = gu;
+        gedges[2 * e + 1] = gv;
+    }
+}
+
+}  // namespace
+}  // namespace etl
+
+using namespace etl;
+
+extern "C" etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
+                                   void *stream) {
+    if (n < 1 || n > (1 << 30) || m < 0 || m > int64_t(INT32_MAX) - 1) return ETL_EINVAL;
+    if (m == 0) return ETL_OK;
+    if (!edges || !is_bridge) return ETL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    int32_t *st = status ? status : ws.get<int32_t>(1);
+    if (!ws.ok()) return ETL_ENOMEM;
+    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    return bridges_core(edges, m, n, is_bridge, st, ws);
+}
+
+extern "C" etl_status find_bridges_batch(const int32_t *edges, const int32_t *edge_off, const int32_t *node_off,
+                                         int32_t k, int64_t total_m, int32_t total_n, uint8_t *is_bridge,
+                                         int32_t *status, void *stream) {
+    if (k < 1 || total_n < k || total_n > (1 << 30) || total_m < 0 || total_m > int64_t(INT32_MAX) - 1)
+        return ETL_EINVAL;
+    if (!edge_off || !node_off) return ETL_EINVAL;
+    if (total_m == 0) return ETL_OK;
+    if (!edges || !is_bridge) return ETL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    int32_t *st = status ? status : ws.get<int32_t>(1);
+    int32_t *bad = ws.get<int32_t>(1);
+    int32_t *gedges = ws.get<int32_t>(2 * total_m);
+    if (!ws.ok()) return ETL_ENOMEM;
+    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
+    {
+        PhaseTimer pt("br.globalize", s);
+        k_check_batch<<<grid_for(k, 256), 256, 0, s>>>(edge_off, node_off, k, total_m, total_n, bad, st);
+        note_launch();
+        k_globalize<<<grid_for(total_m, 256), 256, 0, s>>>(edges, total_m, edge_off, node_off, k, bad, gedges, st);
+        note_launch();
+    }
+    etl_status rc = last_launch();
+    if (rc) return rc;
+    return bridges_core(gedges, total_m, total_n, is_bridge, st, ws);
 }

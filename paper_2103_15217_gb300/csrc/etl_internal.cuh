@@ -140,6 +140,12 @@ struct RankParams {
 };
 RankParams &rank_params();
 
+struct RmqParams {
+    int levels_per_pass = 3;  // 1..3 levels built by one streaming pass
+    int block = 256;          // threads per block of the level kernel
+};
+RmqParams &rmq_params();
+
 // succ[0..n_cap) with elements >= *d_len (if d_len) inert; head = *d_head.
 // dual: also count even-indexed elements (the opening brackets of a tour).
 etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, const int32_t *d_head, bool dual,
@@ -160,17 +166,20 @@ __device__ __forceinline__ int32_t evens_before(const RankResult &r, uint2 p) {
 // Full sparse table over x[0..n): level l holds min (or max) of x[i .. i+2^l)
 // (entries past the end are folded with the identity). levels =
 // floor(log2(max_len)) + 1 where max_len is the longest range ever queried.
-// Level 0 must already be in table[0..n).
+// Level 0 must already be in table[0..n); rows are sparse_ld(n) apart and the
+// build pads each row's tail with the identity.
 int sparse_levels(int64_t max_len);
+// row length (entries) of a table over n entries: n rounded up to a multiple of 4
+int64_t sparse_ld(int64_t n);
 template <bool IS_MAX>
 etl_status sparse_table_build(int32_t *table, int64_t n, int levels, cudaStream_t s);
 
 template <bool IS_MAX>
-__device__ __forceinline__ int32_t sparse_query(const int32_t *__restrict__ table, int64_t n, int32_t lo,
-                                                int32_t hi) {  // inclusive range, lo <= hi
+__device__ __forceinline__ int32_t sparse_query(const int32_t *__restrict__ table, int64_t ld, int32_t lo,
+                                                int32_t hi) {  // inclusive range, lo <= hi; ld = row length
     int len = hi - lo + 1;
     int l = 31 - __clz(len);
-    const int32_t *t = table + int64_t(l) * n;
+    const int32_t *t = table + int64_t(l) * ld;
     int32_t a = __ldg(t + lo), b = __ldg(t + hi - (1 << l) + 1);
     return IS_MAX ? max(a, b) : min(a, b);
 }
@@ -179,10 +188,13 @@ __device__ __forceinline__ int32_t sparse_query(const int32_t *__restrict__ tabl
 
 // ----------------------------------------------------------------- the LCA handle
 struct etl_lca_s {
-    int32_t n = 0;
+    int32_t n = 0;       // nodes (all instances of a batch together)
+    int32_t k = 1;       // trees in the handle
+    int32_t *node_off = nullptr;  // batch only: k+1 instance offsets (device)
     int levels = 0;
     cudaStream_t stream = nullptr;
     int32_t *pre = nullptr, *depth = nullptr, *size = nullptr, *order = nullptr;
-    int32_t *table = nullptr;   // levels * n
+    int64_t ld = 0;             // row length of the sparse table
+    int32_t *table = nullptr;   // levels * ld
     int32_t *status = nullptr;  // device status word
 };

@@ -1,27 +1,33 @@
 // Lowest common ancestors by RMQ over the Euler tour (Sec. 3.1), for a tree
-// given as a parent array (the input format of Sec. 3.2).
+// given as a parent array (the input format of Sec. 3.2), or for a batch of
+// independent trees preprocessed and queried together.
 //
 // Preprocessing (all on one stream, no host synchronisation):
-//   1. k_count_children: child counts, root detection, validation.
+//   1. k_count_children: child counts, roots, validation (and, for a batch,
+//      local parent ids turned into global ones: node v of instance i has
+//      global id node_off[i] + v).
 //   2. scan -> CSR offsets; stable radix sort of (parent, child) -> children of
 //      each node in ascending label order (the grouping step of Sec. 2.1).
 //   3. k_tour_succ: successor array of the Euler tour in bracket form. Node v
 //      owns two list elements, 2v (the arc entering v from its parent, an
-//      opening bracket) and 2v+1 (the arc leaving v, a closing bracket); the
-//      root's two brackets start and end the list. succ(2v) = 2*firstchild(v)
-//      or 2v+1; succ(2c+1) = 2*nextsibling(c) or 2*parent(c)+1. This is
-//      succ(e) = next(twin(e)) of Sec. 2.1 with the cyclic list already cut at
-//      the root (head = 2*root).
+//      opening bracket) and 2v+1 (the arc leaving v, a closing bracket).
+//      succ(2v) = 2*firstchild(v) or 2v+1; succ(2c+1) = 2*nextsibling(c) or
+//      2*parent(c)+1. This is succ(e) = next(twin(e)) of Sec. 2.1 with the
+//      cyclic list cut at the root: the root's two brackets start and end
+//      its tour. k_link_roots chains the tours of a batch, root i's closing
+//      bracket -> root i+1's opening bracket, so one list covers all trees.
 //   4. list ranking (rank.cu), counting opening brackets on the way.
 //   5. k_node_stats: preorder = opening brackets before 2v; depth =
 //      2*pre - rank(2v) (opening minus closing brackets before it, the +1/-1
-//      prefix sum of Sec. 2); size = (rank(2v+1) - rank(2v) + 1) / 2.
+//      prefix sum of Sec. 2); size = (rank(2v+1) - rank(2v) + 1) / 2. In a
+//      chained batch, tree i occupies preorder positions node_off[i] ..
+//      node_off[i+1]-1 and depth / size come out per tree.
 //   6. k_parent_pre: Q[pre(v)] = pre(parent(v)), level 0 of the sparse table.
-//   7. sparse table over Q (rmq.cu).
+//   7. sparse table over Q (rmq.cu), as many levels as the largest tree needs.
 //
 // Query: for u != v with i = min(pre u, pre v), j = max(...), every node with
 // preorder in (i, j] is a proper descendant of LCA(u, v), and the child of the
-// LCA on the path to the deeper end lies in that range; so the minimum of Q
+// LCA on the path to the later end lies in that range; so the minimum of Q
 // over (i, j] is pre(LCA). This is the depth-minimum of the RMQ reduction
 // (the node of least depth in the range is a child of the LCA) with the
 // answer read directly: one min, no argmin and no tie-breaking.
@@ -32,36 +38,83 @@
 namespace etl {
 namespace {
 
-__global__ void k_count_children(const int32_t *__restrict__ parent, int32_t n, int32_t *__restrict__ cnt,
-                                 int32_t *__restrict__ misc, int32_t *__restrict__ status) {
-    // misc[0] = number of roots, misc[1] = root, misc[2] = list head (2*root)
-    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
-        const int32_t p = parent[v];
-        if (p == -1) {
-            atomicAdd(&misc[0], 1);
-            misc[1] = int32_t(v);
-            misc[2] = 2 * int32_t(v);
-        } else if (p < 0 || p >= n) {
-            set_status(status, ETL_EBADTREE);
-        } else {
-            if (p == v) set_status(status, ETL_EBADTREE);
-            atomicAdd(&cnt[p], 1);
+__device__ __forceinline__ int64_t gtid() { return blockIdx.x * int64_t(blockDim.x) + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return int64_t(gridDim.x) * blockDim.x; }
+
+// node_off must be 0 = off[0] < off[1] < ... < off[k] = total (every instance non-empty)
+__global__ void k_check_offsets(const int32_t *__restrict__ off, int32_t k, int32_t total,
+                                int32_t *__restrict__ bad, int32_t *__restrict__ status) {
+    for (int64_t i = gtid(); i < k; i += gstride()) {
+        const int32_t b = off[i], e = off[i + 1];
+        if (b < 0 || e > total || b >= e || (i == 0 && b != 0) || (i == k - 1 && e != total)) {
+            set_status(status, ETL_EINVAL);
+            *bad = 1;
         }
     }
 }
 
+// inst_of[v] = instance of node v; one block per instance, coalesced writes
+__global__ void k_fill_inst(const int32_t *__restrict__ off, int32_t k, const int32_t *__restrict__ bad,
+                            int32_t *__restrict__ inst_of) {
+    if (*bad) return;
+    for (int64_t i = blockIdx.x; i < k; i += gridDim.x) {
+        const int32_t b = off[i], e = off[i + 1];
+        for (int32_t v = b + threadIdx.x; v < e; v += blockDim.x) inst_of[v] = int32_t(i);
+    }
+}
+
+template <bool BATCH>
+__global__ void k_count_children(const int32_t *__restrict__ parent, int32_t n, const int32_t *__restrict__ off,
+                                 const int32_t *__restrict__ inst_of, const int32_t *__restrict__ bad,
+                                 int32_t *__restrict__ gparent, int32_t *__restrict__ cnt,
+                                 int32_t *__restrict__ root_cnt, int32_t *__restrict__ root_of,
+                                 int32_t *__restrict__ status) {
+    const bool bad_offsets = BATCH && *bad;
+    for (int64_t t = gtid(); t < n; t += gstride()) {
+        const int32_t v = int32_t(t);
+        if (bad_offsets) {  // instance ids unusable: drop every node (status is already set)
+            gparent[v] = -2;
+            continue;
+        }
+        const int32_t p = parent[v];
+        int32_t inst = 0, base = 0, size = n;
+        if (BATCH) {
+            inst = inst_of[v];
+            base = off[inst];
+            size = off[inst + 1] - base;
+        }
+        int32_t g = -2;
+        if (p == -1) {
+            atomicAdd(&root_cnt[inst], 1);
+            root_of[inst] = v;
+            g = -1;
+        } else if (p < 0 || p >= size) {
+            set_status(status, ETL_EBADTREE);
+        } else {
+            g = p + base;
+            if (g == v) set_status(status, ETL_EBADTREE);
+            atomicAdd(&cnt[g], 1);
+        }
+        if (BATCH) gparent[v] = g;
+    }
+}
+
+// exactly one root per instance; the list starts at the first root's opening bracket
+__global__ void k_check_roots(const int32_t *__restrict__ root_cnt, const int32_t *__restrict__ root_of, int32_t k,
+                              int32_t *__restrict__ head, int32_t *__restrict__ status) {
+    for (int64_t i = gtid(); i < k; i += gstride())
+        if (root_cnt[i] != 1) set_status(status, ETL_EBADTREE);
+    if (gtid() == 0) *head = 2 * root_of[0];
+}
+
 __global__ void k_tour_succ(const int32_t *__restrict__ keys, const int32_t *__restrict__ kids,
-                            const int32_t *__restrict__ coff, int32_t n, const int32_t *__restrict__ misc,
-                            int32_t *__restrict__ succ, int32_t *__restrict__ status) {
+                            const int32_t *__restrict__ coff, int32_t n, int32_t *__restrict__ succ) {
     const int32_t kept = coff[n];  // number of (parent, child) pairs
-    if (blockIdx.x == 0 && threadIdx.x == 0 && misc[0] != 1) set_status(status, ETL_EBADTREE);
-    const int32_t root = misc[1];
-    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+    for (int64_t t = gtid(); t < n; t += gstride()) {
         const int32_t v = int32_t(t);
         const int32_t b = coff[v], e = coff[v + 1];
         succ[2 * v] = (b < e) ? 2 * kids[b] : 2 * v + 1;  // enter v -> enter first child, or leave v
-        if (v == root) succ[2 * v + 1] = ETL_END;
-        if (t < kept) {  // position t of the grouped children
+        if (t < kept) {                                    // position t of the grouped children
             const int32_t c = kids[t], p = keys[t];
             if (c >= 0 && c < n && p >= 0 && p < n) {
                 const int32_t sib = (t + 1 < coff[p + 1]) ? kids[t + 1] : -1;
@@ -71,12 +124,20 @@ __global__ void k_tour_succ(const int32_t *__restrict__ keys, const int32_t *__r
     }
 }
 
-__global__ void k_node_stats(RankResult rr, int32_t n, const int32_t *__restrict__ misc,
-                             int32_t *__restrict__ pre, int32_t *__restrict__ depth, int32_t *__restrict__ size,
-                             int32_t *__restrict__ order, int32_t *__restrict__ status) {
+// leave root i -> enter root i+1 (or end of the list after the last tree)
+__global__ void k_link_roots(const int32_t *__restrict__ root_of, int32_t k, int32_t n, int32_t *__restrict__ succ) {
+    for (int64_t i = gtid(); i < k; i += gstride()) {
+        const int32_t r = root_of[i];
+        if (r < 0 || r >= n) continue;
+        const int32_t nr = (i + 1 < k) ? root_of[i + 1] : -1;
+        succ[2 * r + 1] = (nr >= 0 && nr < n) ? 2 * nr : ETL_END;
+    }
+}
+
+__global__ void k_node_stats(RankResult rr, int32_t n, int32_t *__restrict__ pre, int32_t *__restrict__ depth,
+                             int32_t *__restrict__ size, int32_t *__restrict__ order, int32_t *__restrict__ status) {
     const uint4 *pk = reinterpret_cast<const uint4 *>(rr.packed);  // brackets 2v and 2v+1 side by side
-    const int32_t root = misc[1];
-    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+    for (int64_t t = gtid(); t < n; t += gstride()) {
         const uint4 q = pk[t];
         if (q.x >= rr.rcap || q.z >= rr.rcap) {  // not on the list from the root: malformed input
             set_status(status, ETL_EBADTREE);
@@ -90,72 +151,94 @@ __global__ void k_node_stats(RankResult rr, int32_t n, const int32_t *__restrict
         depth[t] = 2 * p - r0;
         size[t] = (r1 - r0 + 1) >> 1;
         if (p >= 0 && p < n) order[p] = int32_t(t);
-        if (t == root && (r0 != 0 || int64_t(r1) != 2 * int64_t(n) - 1)) set_status(status, ETL_EBADTREE);
+    }
+}
+
+// root i must open its tree at preorder off[i] and span the whole instance
+__global__ void k_check_instances(const int32_t *__restrict__ root_of, const int32_t *__restrict__ off, int32_t k,
+                                  int32_t n, const int32_t *__restrict__ pre, const int32_t *__restrict__ size,
+                                  int32_t *__restrict__ status) {
+    for (int64_t i = gtid(); i < k; i += gstride()) {
+        const int32_t b = off ? off[i] : 0, e = off ? off[i + 1] : n;
+        const int32_t r = root_of[i];
+        if (r < 0 || r >= n || pre[r] != b || size[r] != e - b) set_status(status, ETL_EBADTREE);
     }
 }
 
 __global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *__restrict__ pre, int32_t n,
                              int32_t *__restrict__ q0) {
-    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+    for (int64_t v = gtid(); v < n; v += gstride()) {
         const int32_t i = pre[v], p = parent[v];
         if (i >= 0 && i < n) q0[i] = (p >= 0 && p < n) ? __ldg(pre + p) : -1;
     }
 }
 
 struct LcaView {
-    int32_t n;
-    const int32_t *pre, *order, *table, *hstatus;
+    int32_t n, k, levels;
+    int64_t ld;
+    const int32_t *pre, *order, *table, *hstatus, *off;
 };
 
 constexpr int kQueryIlp = 4;
 
 // Each thread answers kQueryIlp queries at once so that their dependent
-// gathers (pre, table, order) overlap in flight.
+// gathers (pre, table, order) overlap in flight. BATCH: ids are local to the
+// instance inst[i] and so is the answer.
+template <bool BATCH>
 __global__ void __launch_bounds__(256)
-    k_lca_query(LcaView h, const int32_t *__restrict__ u, const int32_t *__restrict__ v, int64_t q,
-                int32_t *__restrict__ out, int32_t *__restrict__ status) {
+    k_lca_query(LcaView h, const int32_t *__restrict__ inst, const int32_t *__restrict__ u,
+                const int32_t *__restrict__ v, int64_t q, int32_t *__restrict__ out, int32_t *__restrict__ status) {
     const bool bad_tree = *h.hstatus != 0;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t base = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; base < q; base += stride * kQueryIlp) {
-        int32_t a[kQueryIlp], b[kQueryIlp], lo[kQueryIlp], hi[kQueryIlp], res[kQueryIlp];
-        bool need[kQueryIlp];
+    const int64_t stride = gstride();
+    for (int64_t base = gtid(); base < q; base += stride * kQueryIlp) {
+        int32_t a[kQueryIlp], b[kQueryIlp], lo[kQueryIlp], hi[kQueryIlp], res[kQueryIlp], ofs[kQueryIlp];
+        bool need[kQueryIlp], ok[kQueryIlp];
 #pragma unroll
         for (int k = 0; k < kQueryIlp; ++k) {
             const int64_t i = base + k * stride;
             need[k] = false;
+            ok[k] = false;
             res[k] = -1;
+            ofs[k] = 0;
+            a[k] = b[k] = 0;
             if (i < q) {
                 a[k] = __ldcs(u + i);
                 b[k] = __ldcs(v + i);
-            } else {
-                a[k] = b[k] = 0;
+                int32_t lim = h.n;
+                if (BATCH) {
+                    const int32_t t = __ldcs(inst + i);
+                    if (t >= 0 && t < h.k) {
+                        ofs[k] = __ldg(h.off + t);
+                        lim = __ldg(h.off + t + 1) - ofs[k];
+                    } else {
+                        lim = 0;
+                    }
+                }
+                ok[k] = a[k] >= 0 && a[k] < lim && b[k] >= 0 && b[k] < lim;
+                if (!ok[k]) set_status(status, ETL_EBADQUERY);
             }
         }
 #pragma unroll
         for (int k = 0; k < kQueryIlp; ++k) {
-            const int64_t i = base + k * stride;
-            if (i >= q) continue;
-            if (a[k] < 0 || a[k] >= h.n || b[k] < 0 || b[k] >= h.n) {
-                set_status(status, ETL_EBADQUERY);
-            } else if (!bad_tree) {
-                if (a[k] == b[k]) {
-                    res[k] = a[k];
-                } else {
-                    const int32_t pa = __ldg(h.pre + a[k]), pb = __ldg(h.pre + b[k]);
-                    lo[k] = min(pa, pb) + 1;
-                    hi[k] = max(pa, pb);
-                    need[k] = true;
-                }
+            if (!ok[k] || bad_tree) continue;
+            if (a[k] == b[k]) {
+                res[k] = a[k];
+            } else {
+                const int32_t pa = __ldg(h.pre + ofs[k] + a[k]), pb = __ldg(h.pre + ofs[k] + b[k]);
+                lo[k] = min(pa, pb) + 1;
+                hi[k] = max(pa, pb);
+                need[k] = (31 - __clz(hi[k] - lo[k] + 1)) < h.levels;  // cannot fail unless max_n was understated
+                if (!need[k]) set_status(status, ETL_EINVAL);
             }
         }
 #pragma unroll
         for (int k = 0; k < kQueryIlp; ++k)
-            if (need[k]) lo[k] = sparse_query<false>(h.table, h.n, lo[k], hi[k]);
+            if (need[k]) lo[k] = sparse_query<false>(h.table, h.ld, lo[k], hi[k]);
 #pragma unroll
         for (int k = 0; k < kQueryIlp; ++k) {
             const int64_t i = base + k * stride;
             if (i >= q) continue;
-            if (need[k]) res[k] = __ldg(h.order + lo[k]);
+            if (need[k]) res[k] = __ldg(h.order + lo[k]) - ofs[k];
             __stcs(out + i, res[k]);
         }
     }
@@ -171,75 +254,98 @@ int grid_for(int64_t work, int threads) {
 void free_handle(etl_lca_s *h) {
     if (!h) return;
     cudaStream_t s = h->stream;
-    for (int32_t *p : {h->pre, h->depth, h->size, h->order, h->table, h->status})
+    for (int32_t *p : {h->pre, h->depth, h->size, h->order, h->table, h->status, h->node_off})
         if (p) cudaFreeAsync(p, s);
     delete h;
 }
 
-}  // namespace
-}  // namespace etl
-
-using namespace etl;
-
-extern "C" etl_status lca_preprocess(const int32_t *parent, int32_t n, void *stream, etl_lca_t *out) {
-    if (!out) return ETL_EINVAL;
-    *out = nullptr;
-    if (!parent || n < 1 || n > (1 << 30)) return ETL_EINVAL;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+// n nodes in k >= 1 trees; node_off (device, k+1 entries) is null for one tree
+etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, int32_t k, int32_t max_n,
+                     cudaStream_t s, etl_lca_t *out) {
+    const bool batch = node_off != nullptr;
     etl_lca_s *h = new etl_lca_s;
     h->n = n;
+    h->k = k;
     h->stream = s;
-    h->levels = n > 1 ? sparse_levels(n - 1) : 1;
+    h->levels = max_n > 1 ? sparse_levels(max_n - 1) : 1;
+    h->ld = sparse_ld(n);
     const size_t nb = size_t(n) * sizeof(int32_t);
     bool ok = cudaMallocAsync((void **)&h->pre, nb, s) == cudaSuccess;
     ok = ok && cudaMallocAsync((void **)&h->depth, nb, s) == cudaSuccess;
     ok = ok && cudaMallocAsync((void **)&h->size, nb, s) == cudaSuccess;
     ok = ok && cudaMallocAsync((void **)&h->order, nb, s) == cudaSuccess;
-    ok = ok && cudaMallocAsync((void **)&h->table, nb * size_t(h->levels), s) == cudaSuccess;
+    ok = ok && cudaMallocAsync((void **)&h->table, size_t(h->ld) * sizeof(int32_t) * size_t(h->levels), s) ==
+                   cudaSuccess;
     ok = ok && cudaMallocAsync((void **)&h->status, sizeof(int32_t), s) == cudaSuccess;
+    if (ok && batch)
+        ok = cudaMallocAsync((void **)&h->node_off, size_t(k + 1) * sizeof(int32_t), s) == cudaSuccess;
     if (!ok) {
         free_handle(h);
         return ETL_ENOMEM;
     }
     cudaMemsetAsync(h->status, 0, sizeof(int32_t), s);
+    if (batch) cudaMemcpyAsync(h->node_off, node_off, size_t(k + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     etl_status st = ETL_OK;
     {
         Workspace ws(s);
         int32_t *cnt = ws.get<int32_t>(n);
         int32_t *coff = ws.get<int32_t>(int64_t(n) + 1);
-        int32_t *misc = ws.get<int32_t>(4);
+        int32_t *misc = ws.get<int32_t>(4);  // [0] list head, [1] offsets invalid
         int32_t *succ = ws.get<int32_t>(2 * int64_t(n));
+        int32_t *root_cnt = ws.get<int32_t>(k), *root_of = ws.get<int32_t>(k);
+        int32_t *inst_of = batch ? ws.get<int32_t>(n) : nullptr;
+        int32_t *gparent = batch ? ws.get<int32_t>(n) : nullptr;
         if (!ws.ok()) st = ETL_ENOMEM;
+        const int32_t *par = batch ? gparent : parent;
         if (!st) {
             cudaMemsetAsync(cnt, 0, nb, s);
             cudaMemsetAsync(misc, 0, 4 * sizeof(int32_t), s);
+            cudaMemsetAsync(root_cnt, 0, size_t(k) * sizeof(int32_t), s);
+            cudaMemsetAsync(root_of, 0, size_t(k) * sizeof(int32_t), s);
             PhaseTimer pt("lca.count", s);
-            k_count_children<<<grid_for(n, 256), 256, 0, s>>>(parent, n, cnt, misc, h->status);
-        note_launch();
+            if (batch) {
+                k_check_offsets<<<grid_for(k, 256), 256, 0, s>>>(h->node_off, k, n, misc + 1, h->status);
+                note_launch();
+                k_fill_inst<<<k < 8192 ? k : 8192, 256, 0, s>>>(h->node_off, k, misc + 1, inst_of);
+                note_launch();
+                k_count_children<true><<<grid_for(n, 256), 256, 0, s>>>(parent, n, h->node_off, inst_of, misc + 1,
+                                                                        gparent, cnt, root_cnt, root_of, h->status);
+                note_launch();
+            } else {
+                k_count_children<false><<<grid_for(n, 256), 256, 0, s>>>(parent, n, nullptr, nullptr, nullptr,
+                                                                         nullptr, cnt, root_cnt, root_of, h->status);
+                note_launch();
+            }
+            k_check_roots<<<grid_for(k, 256), 256, 0, s>>>(root_cnt, root_of, k, misc, h->status);
+            note_launch();
             st = last_launch();
         }
         if (!st) st = scan_exclusive_i32(cnt, coff, n, ws);
         SortResult sr{};
-        if (!st) st = radix_sort_pairs(parent, nullptr, nullptr, n, ceil_log2(uint64_t(n)), n, ws, &sr);
+        if (!st) st = radix_sort_pairs(par, nullptr, nullptr, n, ceil_log2(uint64_t(n)), n, ws, &sr);
         if (!st) {
             PhaseTimer pt("lca.succ", s);
-            k_tour_succ<<<grid_for(n, 256), 256, 0, s>>>(sr.keys, sr.vals, coff, n, misc, succ, h->status);
-        note_launch();
+            k_tour_succ<<<grid_for(n, 256), 256, 0, s>>>(sr.keys, sr.vals, coff, n, succ);
+            note_launch();
+            k_link_roots<<<grid_for(k, 256), 256, 0, s>>>(root_of, k, n, succ);
+            note_launch();
             st = last_launch();
         }
         RankResult rr{};
-        if (!st) st = list_rank(succ, 2 * int64_t(n), nullptr, misc + 2, true, 2 * int64_t(n), h->status, ws, &rr);
+        if (!st) st = list_rank(succ, 2 * int64_t(n), nullptr, misc, true, 2 * int64_t(n), h->status, ws, &rr);
         if (!st) {
             PhaseTimer pt("lca.node_stats", s);
-            k_node_stats<<<grid_for(n, 256), 256, 0, s>>>(rr, n, misc, h->pre, h->depth, h->size, h->order,
-                                                          h->status);
-        note_launch();
+            k_node_stats<<<grid_for(n, 256), 256, 0, s>>>(rr, n, h->pre, h->depth, h->size, h->order, h->status);
+            note_launch();
+            k_check_instances<<<grid_for(k, 256), 256, 0, s>>>(root_of, batch ? h->node_off : nullptr, k, n, h->pre,
+                                                                h->size, h->status);
+            note_launch();
             st = last_launch();
         }
         if (!st) {
             PhaseTimer pt("lca.parent_pre", s);
-            k_parent_pre<<<grid_for(n, 256), 256, 0, s>>>(parent, h->pre, n, h->table);
-        note_launch();
+            k_parent_pre<<<grid_for(n, 256), 256, 0, s>>>(par, h->pre, n, h->table);
+            note_launch();
             st = last_launch();
         }
         if (!st) st = sparse_table_build<false>(h->table, n, h->levels, s);
@@ -252,17 +358,54 @@ extern "C" etl_status lca_preprocess(const int32_t *parent, int32_t n, void *str
     return ETL_OK;
 }
 
+etl_status query_launch(etl_lca_t h, const int32_t *inst, const int32_t *u, const int32_t *v, int64_t q,
+                        int32_t *out, int32_t *status, cudaStream_t s) {
+    LcaView view{h->n, h->k, h->levels, h->ld, h->pre, h->order, h->table, h->status, h->node_off};
+    PhaseTimer pt("lca.query", s);
+    const int grid = grid_for(ceil_div(q, kQueryIlp), 256);
+    if (inst)
+        k_lca_query<true><<<grid, 256, 0, s>>>(view, inst, u, v, q, out, status);
+    else
+        k_lca_query<false><<<grid, 256, 0, s>>>(view, nullptr, u, v, q, out, status);
+    note_launch();
+    return last_launch();
+}
+
+}  // namespace
+}  // namespace etl
+
+using namespace etl;
+
+extern "C" etl_status lca_preprocess(const int32_t *parent, int32_t n, void *stream, etl_lca_t *out) {
+    if (!out) return ETL_EINVAL;
+    *out = nullptr;
+    if (!parent || n < 1 || n > (1 << 30)) return ETL_EINVAL;
+    return lca_build(parent, n, nullptr, 1, n, static_cast<cudaStream_t>(stream), out);
+}
+
+extern "C" etl_status lca_preprocess_batch(const int32_t *parent, const int32_t *node_off, int32_t k,
+                                           int32_t total_n, int32_t max_n, void *stream, etl_lca_t *out) {
+    if (!out) return ETL_EINVAL;
+    *out = nullptr;
+    if (!parent || !node_off || k < 1 || total_n < k || total_n > (1 << 30) || max_n < 1 || max_n > total_n)
+        return ETL_EINVAL;
+    return lca_build(parent, total_n, node_off, k, max_n, static_cast<cudaStream_t>(stream), out);
+}
+
 extern "C" etl_status lca_query(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q, int32_t *out,
                                 int32_t *status, void *stream) {
-    if (!h || q < 0 || q > (int64_t(1) << 40)) return ETL_EINVAL;
+    if (!h || h->node_off || q < 0 || q > (int64_t(1) << 40)) return ETL_EINVAL;
     if (q == 0) return ETL_OK;
     if (!u || !v || !out) return ETL_EINVAL;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    LcaView view{h->n, h->pre, h->order, h->table, h->status};
-    PhaseTimer pt("lca.query", s);
-    k_lca_query<<<grid_for(ceil_div(q, kQueryIlp), 256), 256, 0, s>>>(view, u, v, q, out, status);
-        note_launch();
-    return last_launch();
+    return query_launch(h, nullptr, u, v, q, out, status, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" etl_status lca_query_batch(etl_lca_t h, const int32_t *inst, const int32_t *u, const int32_t *v,
+                                      int64_t q, int32_t *out, int32_t *status, void *stream) {
+    if (!h || !h->node_off || q < 0 || q > (int64_t(1) << 40)) return ETL_EINVAL;
+    if (q == 0) return ETL_OK;
+    if (!inst || !u || !v || !out) return ETL_EINVAL;
+    return query_launch(h, inst, u, v, q, out, status, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" etl_status lca_status(etl_lca_t h, int32_t *status) {

@@ -1,10 +1,17 @@
 // Sparse tables for range-minimum / range-maximum queries (Sec. 3.1 reduces
-// LCA to RMQ; Sec. 4.1 aggregates low / high over subtrees by RMQ). Level l
-// is built from level l-1 by one coalesced streaming pass:
-//     T_l[i] = op(T_{l-1}[i], T_{l-1}[i + 2^(l-1)]).
-// The second operand trails the first by 2^(l-1) entries, which the 129 MB L2
-// still holds for every level of the sizes used here, so each level costs
-// about one DRAM read and one DRAM write per entry.
+// LCA to RMQ; Sec. 4.1 aggregates low / high over subtrees by RMQ).
+//
+// Level l holds op over x[i .. i + 2^l). One streaming pass builds up to three
+// consecutive levels l, l+1, l+2 from level l-1: with h = 2^(l-1),
+//     T_l[i]   = op(p[i], p[i+h])
+//     T_l+1[i] = op(p[i], p[i+h], p[i+2h], p[i+3h])
+//     T_l+2[i] = op(p[i] .. p[i+7h] in steps of h)
+// where p = T_(l-1). Every thread handles four consecutive entries with int4
+// loads and stores; shifted operands whose offset is not a multiple of four
+// are assembled from two aligned int4 loads. Only the unshifted stream comes
+// from DRAM; the shifted ones trail it by at most 7h entries and hit in the
+// 129 MB L2 for the sizes used here. Rows are padded to a multiple of four
+// entries with the identity.
 #include <climits>
 
 #include "etl_internal.cuh"
@@ -18,33 +25,62 @@ __device__ __forceinline__ int32_t op(int32_t a, int32_t b) {
 }
 
 template <bool IS_MAX>
-__global__ void k_level_vec4(int32_t *__restrict__ table, int64_t n, int l) {
-    // n % 4 == 0 and 2^(l-1) % 4 == 0: whole int4 vectors
-    const int32_t ident = IS_MAX ? INT_MIN : INT_MAX;
-    const int4 *prev = reinterpret_cast<const int4 *>(table + int64_t(l - 1) * n);
-    int4 *cur = reinterpret_cast<int4 *>(table + int64_t(l) * n);
-    const int64_t nv = n >> 2, hv = (int64_t(1) << (l - 1)) >> 2;
+__device__ __forceinline__ int4 op4(int4 a, int4 b) {
+    return make_int4(op<IS_MAX>(a.x, b.x), op<IS_MAX>(a.y, b.y), op<IS_MAX>(a.z, b.z), op<IS_MAX>(a.w, b.w));
+}
+
+// elements [4i + s, 4i + s + 4) of a padded row (nv int4 vectors), identity past the end
+template <bool IS_MAX>
+__device__ __forceinline__ int4 shifted(const int4 *__restrict__ p, int64_t i, int64_t s, int64_t nv) {
+    const int32_t id = IS_MAX ? INT_MIN : INT_MAX;
+    const int4 I = make_int4(id, id, id, id);
+    const int64_t q = i + (s >> 2);
+    const int r = int(s & 3);
+    const int4 a = q < nv ? p[q] : I;
+    if (r == 0) return a;
+    const int4 b = q + 1 < nv ? p[q + 1] : I;
+    if (r == 1) return make_int4(a.y, a.z, a.w, b.x);
+    if (r == 2) return make_int4(a.z, a.w, b.x, b.y);
+    return make_int4(a.w, b.x, b.y, b.z);
+}
+
+template <bool IS_MAX>
+__global__ void __launch_bounds__(1024) k_levels(int32_t *__restrict__ table, int64_t ld, int l, int count) {
+    const int4 *p = reinterpret_cast<const int4 *>(table + int64_t(l - 1) * ld);
+    int4 *o0 = reinterpret_cast<int4 *>(table + int64_t(l) * ld);
+    int4 *o1 = reinterpret_cast<int4 *>(table + int64_t(l + 1) * ld);
+    int4 *o2 = reinterpret_cast<int4 *>(table + int64_t(l + 2) * ld);
+    const int64_t nv = ld >> 2, h = int64_t(1) << (l - 1);
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nv; i += int64_t(gridDim.x) * blockDim.x) {
-        int4 a = prev[i];
-        int4 b = i + hv < nv ? prev[i + hv] : make_int4(ident, ident, ident, ident);
-        cur[i] = make_int4(op<IS_MAX>(a.x, b.x), op<IS_MAX>(a.y, b.y), op<IS_MAX>(a.z, b.z), op<IS_MAX>(a.w, b.w));
+        const int4 m01 = op4<IS_MAX>(p[i], shifted<IS_MAX>(p, i, h, nv));
+        o0[i] = m01;
+        if (count > 1) {
+            const int4 m23 = op4<IS_MAX>(shifted<IS_MAX>(p, i, 2 * h, nv), shifted<IS_MAX>(p, i, 3 * h, nv));
+            const int4 m03 = op4<IS_MAX>(m01, m23);
+            o1[i] = m03;
+            if (count > 2) {
+                const int4 m45 = op4<IS_MAX>(shifted<IS_MAX>(p, i, 4 * h, nv), shifted<IS_MAX>(p, i, 5 * h, nv));
+                const int4 m67 = op4<IS_MAX>(shifted<IS_MAX>(p, i, 6 * h, nv), shifted<IS_MAX>(p, i, 7 * h, nv));
+                o2[i] = op4<IS_MAX>(m03, op4<IS_MAX>(m45, m67));
+            }
+        }
     }
 }
 
 template <bool IS_MAX>
-__global__ void k_level(int32_t *__restrict__ table, int64_t n, int l) {
-    const int32_t ident = IS_MAX ? INT_MIN : INT_MAX;
-    const int32_t *prev = table + int64_t(l - 1) * n;
-    int32_t *cur = table + int64_t(l) * n;
-    const int64_t h = int64_t(1) << (l - 1);
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        int32_t a = prev[i];
-        int32_t b = i + h < n ? prev[i + h] : ident;
-        cur[i] = op<IS_MAX>(a, b);
-    }
+__global__ void k_pad(int32_t *__restrict__ table, int64_t n, int64_t ld) {
+    const int64_t i = n + threadIdx.x;
+    if (i < ld) table[i] = IS_MAX ? INT_MIN : INT_MAX;
 }
 
 }  // namespace
+
+RmqParams &rmq_params() {
+    static RmqParams p;
+    return p;
+}
+
+int64_t sparse_ld(int64_t n) { return (n + 3) & ~int64_t(3); }
 
 int sparse_levels(int64_t max_len) {
     int L = 1;
@@ -54,23 +90,26 @@ int sparse_levels(int64_t max_len) {
 
 template <bool IS_MAX>
 etl_status sparse_table_build(int32_t *table, int64_t n, int levels, cudaStream_t s) {
-    const int grid_cap = num_sms() * 8;
-    for (int l = 1; l < levels; ++l) {
-        const bool vec = (n % 4 == 0) && l >= 3;
-        const int64_t work = vec ? n / 4 : n;
-        int blocks = int(ceil_div(work, 256));
+    const int64_t ld = sparse_ld(n);
+    if (ld > n) {
+        k_pad<IS_MAX><<<1, 4, 0, s>>>(table, n, ld);
+        note_launch();
+    }
+    const RmqParams &R = rmq_params();
+    const int grid_cap = num_sms() * (2048 / R.block);
+    for (int l = 1; l < levels;) {
+        const int count = levels - l >= R.levels_per_pass ? R.levels_per_pass : levels - l;
+        int blocks = int(ceil_div(ld / 4, R.block));
         if (blocks > grid_cap) blocks = grid_cap;
         if (blocks < 1) blocks = 1;
         PhaseTimer pt(IS_MAX ? "rmq.level_max" : "rmq.level_min", s);
-        if (vec)
-            k_level_vec4<IS_MAX><<<blocks, 256, 0, s>>>(table, n, l);
-        else
-            k_level<IS_MAX><<<blocks, 256, 0, s>>>(table, n, l);
+        k_levels<IS_MAX><<<blocks, R.block, 0, s>>>(table, ld, l, count);
         note_launch();
         etl_status st = last_launch();
         if (st) return st;
+        l += count;
     }
-    return ETL_OK;
+    return last_launch();
 }
 
 template etl_status sparse_table_build<false>(int32_t *, int64_t, int, cudaStream_t);

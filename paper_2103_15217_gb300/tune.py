@@ -1,0 +1,139 @@
+"""Autotuner for the launch parameters of the Euler-tour library.
+
+The knobs change no result, only speed (``etl_tune_set``): the list ranker's
+splitter densities and walk-kernel shape, and the sparse-table build's levels
+per pass and block size. ``autotune`` times candidate settings with CUDA
+events on representative inputs -- a tree preprocessing (tour + ranking +
+sparse table) and a bridge-finding call of the requested size -- and keeps
+the fastest. Results are cached per (GPU name, size bucket) in
+``_build/tune_cache.json`` so later runs start from the tuned values.
+
+The search is coordinate-wise: ranking density first (it sets the length of
+the longest dependent walk), then the walk kernel's shape, then the RMQ
+build; each coordinate keeps the best value found before moving on.
+"""
+
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+
+import numpy as np
+import torch
+
+from . import find_bridges, lca_preprocess, load_library, tune_get, tune_set
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json")
+
+SPACE = [
+    ("rank_k0_log2", [2, 3, 4, 5]),
+    ("rank_k_log2", [3, 4, 5]),
+    ("rank_block", [128, 256, 512]),
+    ("rank_blocks_per_sm", [4, 8, 16]),
+    ("rmq_levels_per_pass", [1, 2, 3]),
+    ("rmq_block", [256, 512]),
+]
+
+
+def _bucket(n: int) -> str:
+    return f"2^{max(10, int(math.ceil(math.log2(max(n, 2)))))}"
+
+
+def _key(n: int) -> str:
+    return f"{torch.cuda.get_device_name()}|{_bucket(n)}"
+
+
+def _load_cache() -> dict:
+    try:
+        with open(_CACHE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save_cache(c: dict):
+    os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+    tmp = _CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(c, f, indent=1, sort_keys=True)
+    os.replace(tmp, _CACHE)
+
+
+def _inputs(n: int, seed: int = 7):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    parent = torch.from_numpy(synth.tree_parent(n, None, seed=seed)).to(dev)
+    gn = max(64, n // 4)
+    edges = torch.from_numpy(synth.easy_graph(gn, 8 * gn, seed=seed)).to(dev)
+    return parent, edges, gn
+
+
+def _time(fn, reps: int) -> float:
+    s = torch.cuda.current_stream()
+    fn()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def autotune(n: int = 1 << 22, reps: int = 3, use_cache: bool = True, verbose: bool = False) -> dict:
+    """Tune for trees of about n nodes (and graphs of n/4 nodes, 8 edges per node).
+    Applies the best setting and returns {"params": ..., "ms": ..., "trials": ...}."""
+    load_library()
+    key = _key(n)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        tune_set(**cache[key]["params"])
+        return dict(cache[key], cached=True)
+    parent, edges, gn = _inputs(n)
+
+    def workload():
+        h = lca_preprocess(parent)
+        h.free()
+        find_bridges(edges, gn)
+
+    best = tune_get()
+    tune_set(**best)
+    best_ms = _time(workload, reps)
+    trials = [(dict(best), best_ms)]
+    for name, values in SPACE:
+        for v in values:
+            if v == best[name]:
+                continue
+            cand = dict(best, **{name: v})
+            if cand["rank_block"] * cand["rank_blocks_per_sm"] > 2048:
+                continue
+            try:
+                tune_set(**cand)
+            except Exception:
+                continue
+            ms = _time(workload, reps)
+            trials.append((dict(cand), ms))
+            if verbose:
+                print(f"  {name}={v}: {ms:.3f} ms (best {best_ms:.3f})")
+            if ms < best_ms:
+                best, best_ms = cand, ms
+        tune_set(**best)
+    res = {"params": best, "ms": best_ms, "n": n, "trials": len(trials),
+           "default_ms": trials[0][1]}
+    cache[key] = res
+    _save_cache(cache)
+    return res
+
+
+if __name__ == "__main__":
+    import sys
+    n = int(sys.argv[1]) if len(sys.argv) > 1 else 1 << 22
+    print(json.dumps(autotune(n, use_cache=False, verbose=True)))
