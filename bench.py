@@ -65,13 +65,13 @@ ALGO = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--small", action="store_true", help="small sizes (functional check only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["all", "core", "batched"], default="all",
+    ap.add_argument("--mode", choices=["all", "core", "batched", "serve"], default="all",
                     help="core = the scale workload; batched = 4096 mixed instances, batched vs per-instance")
     ap.add_argument("--case", choices=["lca", "easy", "hard"], default=None,
                     help="run one workload of size --n twice (warm-up + one more) and exit; for profilers")
@@ -125,7 +125,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -286,10 +286,8 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, etl, trees, graphs, dev, units, world)
 
-    if args.mode in ("all", "batched"):
-        batched_res = run_batched(args, dev)
-    else:
-        batched_res = None
+    batched_res = run_batched(args, dev) if args.mode in ("all", "batched") else None
+    serve_res = run_serve(args) if args.mode in ("all", "serve") else None
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -301,6 +299,7 @@ def run_ours(args):
                    "wall_s_timed": wall},
         "breakdown": breakdown,
         "batched": batched_res,
+        "serving": serve_res,
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,
@@ -498,6 +497,64 @@ def run_batched(args, dev):
         "speedup": t_pi / t_b, "results_identical": equal, "unit": UNIT,
         "host_launch_sites_during_replay": launches_b,
     }
+
+
+# ------------------------------------------------------------------ serving
+
+def make_serving_inputs(small: bool, seed: int = 1, nreq: int = 600):
+    import synth
+    from paper_2103_15217_gb300.serve import Request
+    from synth.generators import make_graph
+    if small:
+        trees, descs = synth.serving_stream(seed=seed, nrequests=60, ntrees=8, tree_exp=(10, 13), batch_exp=(4, 12),
+                                            graph_exp=(10, 12))
+    else:
+        trees, descs = synth.serving_stream(seed=seed, nrequests=nreq)
+    parents = [synth.tree_parent(d["n"], d["grasp"], seed=d["seed"]) for d in trees]
+    reqs = []
+    for i, d in enumerate(descs):
+        if d["kind"] == "lca":
+            u, v = synth.lca_queries(trees[d["tree"]]["n"], d["q"], seed=d["seed"])
+            reqs.append(Request("lca", d["t"], tree=d["tree"], u=u, v=v, rid=i))
+        else:
+            e = make_graph(dict(kind=d["graph"], n=d["n"], m=d["m"], seed=d["seed"]))
+            reqs.append(Request("bridges", d["t"], n=d["n"], edges=e, rid=i))
+    return parents, reqs
+
+
+def run_serve(args):
+    """Poisson stream over resident trees: continuous batching vs plain per-request launches."""
+    import torch
+
+    from paper_2103_15217_gb300.serve import Server, summarize
+    parents, reqs = make_serving_inputs(args.small)
+    srv = Server(parents, budget_bytes=40 << 30, slots=4)
+    # offered load: scale arrival times so the stream runs at a multiple of the measured capacity
+    base = [r.t for r in reqs]
+    warm = srv.serve(reqs[: min(40, len(reqs))], batching=True, realtime=False)
+    offline = srv.serve(reqs, batching=True, realtime=False)
+    cap = summarize(offline)
+    span = max(base) - min(base)
+    out = {"workload": (f"{len(parents)} resident trees n log-uniform 2^10..2^22; {len(reqs)} requests, Poisson "
+                        f"arrivals; LCA batches log-uniform 2^4..2^20 queries; 10% bridge requests on fresh graphs "
+                        f"n log-uniform 2^10..2^22, m = 4n, easy/hard; 40 GB budget, 4 slots"),
+           "capacity_units_per_s": cap["throughput"], "loads": {}}
+    units = sum(r.units() for r in reqs)
+    for load in (0.5, 0.8, 1.0, 1.2):
+        target = units / (cap["throughput"] * load)
+        for r, t in zip(reqs, base):
+            r.t = (t - min(base)) / span * target
+        res_b = srv.serve(reqs, batching=True)
+        res_p = srv.serve(reqs, batching=False)
+        same = all((a.out == b.out).all() for a, b in zip(res_b, res_p))
+        out["loads"][str(load)] = {"continuous_batching": summarize(res_b), "per_request": summarize(res_p),
+                                   "results_identical": bool(same)}
+    for r, t in zip(reqs, base):
+        r.t = t
+    srv.close()
+    del warm
+    torch.cuda.synchronize()
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle arm
