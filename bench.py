@@ -87,6 +87,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t: float, world: int, device=None) -> float:
+    """The slowest rank's time: the whole job is as fast as its slowest replica."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank runs its own replica of the workload (weak scaling), with its own inputs."""
+    return 1 + rank
+
+
 # ------------------------------------------------------------------ inputs
 
 def make_inputs(small: bool, seed: int):
@@ -177,7 +193,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     etl.build()
     etl.load_library()
-    trees, graphs = make_inputs(args.small, seed=1 + rank)
+    trees, graphs = make_inputs(args.small, seed=replica_seed(rank))
 
     d_trees = [dict(t, parent_d=torch.from_numpy(t["parent"]).to(dev), u_d=torch.from_numpy(t["u"]).to(dev),
                     v_d=torch.from_numpy(t["v"]).to(dev)) for t in trees]
@@ -259,11 +275,7 @@ def run_ours(args):
             part.setdefault(f"graph.{g['kind']}", []).append(b)
             tot += b
         step_s.append(tot)
-    t_step = sum(step_s) / len(step_s)
-    if world > 1:
-        tt = torch.tensor([t_step], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(sum(step_s) / len(step_s), world, dev)
     value = units * world / t_step
 
     breakdown = {}
