@@ -55,8 +55,8 @@ ALGO = {
     ("lca.query", "tree"): ("query", 32),      # u, v 8; pre 8; two table entries 8; order 4; out 4
     ("sort.scatter", "tree"): ("node", 16),    # read key, value; write key, value
     ("sort.scatter", "graph"): ("arc", 16),
-    ("lca.node_stats", "tree"): ("node", 32),  # read 2 packed 16, gather 2 prefixes 4, write 3x4, order 4 (approx)
-    ("lca.parent_pre", "tree"): ("node", 16),
+    ("lca.node_stats", "tree"): ("node", 32),  # 2 records 16, write pre/depth/size 12, order 4
+    ("lca.parent_pre", "tree"): ("node", 16),  # parent 4, pre 4, pre[parent] 4, Q 4
     ("br.hook", "graph"): ("edge", 17),        # edge 8, flag 1, two root lookups 8
     ("br.lowhigh_prep", "graph"): ("edge", 24),
 }

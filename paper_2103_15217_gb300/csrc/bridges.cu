@@ -6,8 +6,10 @@
 //   root under the smaller one with a CAS. A CAS that succeeds joins two
 //   different trees, so its edge is a forest edge; exactly n - c succeed.
 // Phase 2, Euler tour of the forest (Sec. 2.1): forest edge t owns half-edges
-//   2t = (u_t, v_t) and 2t+1 = (v_t, u_t), so twin(a) = a ^ 1. A stable radix
-//   sort by tail groups the half-edges of every vertex (array B); next(a) is
+//   2t = (u_t, v_t) and 2t+1 = (v_t, u_t), so twin(a) = a ^ 1. A counting
+//   sort by tail (atomic slots; the order inside a vertex's group is free,
+//   any cyclic order gives an Euler tour) groups the half-edges of every
+//   vertex (array B); next(a) is
 //   the following entry of B with the same tail, cyclically; succ(a) =
 //   next(twin(a)). Each component's cyclic list is cut in front of the first
 //   half-edge of its root (the smallest vertex, which is where hooking ends),
@@ -34,11 +36,10 @@ namespace {
 
 constexpr int64_t kFindCap = int64_t(1) << 26;  // bound on pointer-chasing steps of one edge
 
-__global__ void k_init(int32_t n, int32_t *__restrict__ par, int32_t *__restrict__ first_pos,
-                       int32_t *__restrict__ tin) {
+__global__ void k_init(int32_t n, int32_t *__restrict__ par, int32_t *__restrict__ deg, int32_t *__restrict__ tin) {
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
         par[v] = int32_t(v);
-        first_pos[v] = -1;
+        deg[v] = 0;
         tin[v] = 0;
     }
 }
@@ -56,16 +57,18 @@ __device__ __forceinline__ int32_t find_root(int32_t *par, int32_t x, int64_t &b
     return -1;
 }
 
-__global__ void k_hook(const int32_t *__restrict__ edges, int64_t m, int32_t n, int32_t *__restrict__ par,
-                       uint8_t *__restrict__ is_tree, int32_t *__restrict__ status) {
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+__global__ void k_hook(const int32_t *__restrict__ edges, int64_t e0, int64_t e1, int32_t n,
+                       int32_t *__restrict__ par, uint8_t *__restrict__ is_tree, int32_t *__restrict__ status) {
+    for (int64_t e = e0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < e1; e += int64_t(gridDim.x) * blockDim.x) {
         int32_t a = edges[2 * e], b = edges[2 * e + 1];
         uint8_t tree = 0;
         if (a < 0 || a >= n || b < 0 || b >= n) {
             set_status(status, ETL_EBADGRAPH);
         } else {
             int64_t budget = kFindCap;
-            while (true) {
+            // both ends already point at the same node: same set, nothing to hook
+            const bool same = __ldcg(par + a) == __ldcg(par + b);
+            while (!same) {
                 const int32_t ra = find_root(par, a, budget), rb = find_root(par, b, budget);
                 if (ra < 0 || rb < 0) {
                     set_status(status, ETL_ETIMEOUT);
@@ -111,38 +114,45 @@ __global__ void k_forest_edges(const int32_t *__restrict__ edges, int64_t m, con
     }
 }
 
-// first / one-past-last position of each tail in the sorted half-edge array
-__global__ void k_group_bounds(const int32_t *__restrict__ key, const int32_t *__restrict__ d_len,
-                               int32_t *__restrict__ first_pos, int32_t *__restrict__ end_pos) {
+// half-edges per tail vertex
+__global__ void k_arc_count(const int32_t *__restrict__ tuv, const int32_t *__restrict__ d_len,
+                            int32_t *__restrict__ deg) {
     const int64_t len = *d_len;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < len; i += int64_t(gridDim.x) * blockDim.x) {
-        const int32_t k = key[i];
-        if (i == 0 || key[i - 1] != k) first_pos[k] = int32_t(i);
-        if (i == len - 1 || key[i + 1] != k) end_pos[k] = int32_t(i + 1);
+    for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < len; a += int64_t(gridDim.x) * blockDim.x)
+        atomicAdd(&deg[tuv[a]], 1);
+}
+
+// B[i] = (half-edge, tail) grouped by tail: off[x] .. off[x+1]-1 are the half-edges leaving x
+__global__ void k_arc_scatter(const int32_t *__restrict__ tuv, const int32_t *__restrict__ d_len,
+                              const int32_t *__restrict__ off, int32_t *__restrict__ deg, int2 *__restrict__ B) {
+    const int64_t len = *d_len;
+    for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < len; a += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t x = tuv[a];
+        const int32_t k = atomicSub(&deg[x], 1) - 1;
+        B[off[x] + k] = make_int2(int32_t(a), x);
     }
 }
 
 // succ(twin(b)) := next(b) for every half-edge b at position i of B; half-edge
 // slots beyond the forest (and the virtual head, set later) are inert
-__global__ void k_forest_succ(const int32_t *__restrict__ key, const int32_t *__restrict__ B,
-                              const int32_t *__restrict__ d_len, int64_t cap, const int32_t *__restrict__ first_pos,
-                              const int32_t *__restrict__ end_pos, int32_t *__restrict__ succ) {
+__global__ void k_forest_succ(const int2 *__restrict__ B, const int32_t *__restrict__ d_len, int64_t cap,
+                              const int32_t *__restrict__ off, int32_t *__restrict__ succ) {
     const int64_t len = *d_len;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cap; i += int64_t(gridDim.x) * blockDim.x) {
         if (i < len) {
-            const int32_t b = B[i], x = key[i];
-            const int32_t nb = (i + 1 < end_pos[x]) ? B[i + 1] : B[first_pos[x]];
-            succ[b ^ 1] = nb;
+            const int2 bx = B[i];
+            const int32_t nb = (i + 1 < off[bx.y + 1]) ? B[i + 1].x : B[off[bx.y]].x;
+            succ[bx.x ^ 1] = nb;
         } else {
             succ[i] = ETL_END;
         }
     }
 }
 
-__global__ void k_root_flags(int32_t n, const int32_t *__restrict__ par, const int32_t *__restrict__ first_pos,
+__global__ void k_root_flags(int32_t n, const int32_t *__restrict__ par, const int32_t *__restrict__ off,
                              uint8_t *__restrict__ flag) {
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
-        flag[v] = (par[v] == v && first_pos[v] >= 0) ? 1 : 0;
+        flag[v] = (par[v] == v && off[v + 1] > off[v]) ? 1 : 0;
 }
 
 __global__ void k_root_list(int32_t n, const uint8_t *__restrict__ flag, const int32_t *__restrict__ rpos,
@@ -154,14 +164,14 @@ __global__ void k_root_list(int32_t n, const uint8_t *__restrict__ flag, const i
 // cut each component's cyclic tour in front of its root's first half-edge and
 // chain the components: virtual head -> comp 0 -> comp 1 -> ... -> end
 __global__ void k_chain(int32_t n, const int32_t *__restrict__ rpos, const int32_t *__restrict__ roots,
-                        const int32_t *__restrict__ B, const int32_t *__restrict__ first_pos,
-                        const int32_t *__restrict__ end_pos, int32_t vhead, int32_t *__restrict__ succ) {
+                        const int2 *__restrict__ B, const int32_t *__restrict__ off, int32_t vhead,
+                        int32_t *__restrict__ succ) {
     const int32_t c = rpos[n];
-    if (blockIdx.x == 0 && threadIdx.x == 0) succ[vhead] = c > 0 ? B[first_pos[roots[0]]] : ETL_END;
+    if (blockIdx.x == 0 && threadIdx.x == 0) succ[vhead] = c > 0 ? B[off[roots[0]]].x : ETL_END;
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < c; k += int64_t(gridDim.x) * blockDim.x) {
         const int32_t r = roots[k];
-        const int32_t tail = B[end_pos[r] - 1] ^ 1;  // the half-edge whose successor was the head
-        succ[tail] = (k + 1 < c) ? B[first_pos[roots[k + 1]]] : ETL_END;
+        const int32_t tail = B[off[r + 1] - 1].x ^ 1;  // the half-edge whose successor was the head
+        succ[tail] = (k + 1 < c) ? B[off[roots[k + 1]]].x : ETL_END;
     }
 }
 
@@ -189,12 +199,12 @@ __global__ void k_forest_tin(RankResult rr, const int32_t *__restrict__ d_arcs, 
 }
 
 __global__ void k_root_tin(int32_t n, const int32_t *__restrict__ rpos, const int32_t *__restrict__ roots,
-                           const int32_t *__restrict__ B, const int32_t *__restrict__ first_pos, RankResult rr,
+                           const int2 *__restrict__ B, const int32_t *__restrict__ off, RankResult rr,
                            int32_t *__restrict__ tin) {
     const int32_t c = rpos[n];
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < c; k += int64_t(gridDim.x) * blockDim.x) {
         const int32_t r = roots[k];
-        const uint2 p = rr.packed[B[first_pos[r]]];
+        const uint2 p = rr.packed[B[off[r]].x];
         tin[r] = p.x < rr.rcap ? rank_of(rr, p) - 1 : -1;
     }
 }
@@ -216,10 +226,15 @@ __global__ void k_nontree_minmax(const int32_t *__restrict__ edges, int64_t m, i
         const int32_t a = edges[2 * e], b = edges[2 * e + 1];
         if (a < 0 || a >= n || b < 0 || b >= n || a == b) continue;
         const int32_t ta = __ldg(tin + a), tb = __ldg(tin + b);
-        atomicMin(nlo + a, tb);
-        atomicMax(nhi + a, tb);
-        atomicMin(nlo + b, ta);
-        atomicMax(nhi + b, ta);
+        // nlo(x) and nhi(x) start at tin(x): of the four updates only the one lowering the later
+        // end's nlo and the one raising the earlier end's nhi can change anything
+        if (ta < tb) {
+            atomicMax(nhi + a, tb);
+            atomicMin(nlo + b, ta);
+        } else if (tb < ta) {
+            atomicMax(nhi + b, ta);
+            atomicMin(nlo + a, tb);
+        }
     }
 }
 
@@ -290,7 +305,8 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     const int64_t P = N;                    // tour positions 0 .. A
     const int levels = sparse_levels(P);
     const int64_t ld = sparse_ld(P);
-    int32_t *par = ws.get<int32_t>(n), *first_pos = ws.get<int32_t>(n), *end_pos = ws.get<int32_t>(n);
+    int32_t *par = ws.get<int32_t>(n), *deg = ws.get<int32_t>(n), *off = ws.get<int32_t>(int64_t(n) + 1);
+    int2 *B = ws.get<int2>(A > 0 ? A : 1);
     int32_t *tin = ws.get<int32_t>(n), *nlo = ws.get<int32_t>(n), *nhi = ws.get<int32_t>(n);
     uint8_t *is_tree = ws.get<uint8_t>(m), *rflag = ws.get<uint8_t>(n);
     int32_t *tpos = ws.get<int32_t>(m + 1), *rpos = ws.get<int32_t>(int64_t(n) + 1), *roots = ws.get<int32_t>(n);
@@ -305,13 +321,22 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     const int gn = grid_for(n, 256), gm = grid_for(m, 256), gA = grid_for(N, 256);
     {
         PhaseTimer pt("br.init", s);
-        k_init<<<gn, 256, 0, s>>>(n, par, first_pos, tin);
+        k_init<<<gn, 256, 0, s>>>(n, par, deg, tin);
         note_launch();
     }
     {
+        // hook a first slice of the edges, compress every path to its root, then hook the rest:
+        // after the compression most finds take one step and most edges meet equal roots at once
+        const int64_t m1 = m < int64_t(n) ? m : int64_t(n);
         PhaseTimer pt("br.hook", s);
-        k_hook<<<gm, 256, 0, s>>>(edges, m, n, par, is_tree, st);
+        k_hook<<<grid_for(m1, 256), 256, 0, s>>>(edges, 0, m1, n, par, is_tree, st);
         note_launch();
+        if (m1 < m) {
+            k_compress<<<gn, 256, 0, s>>>(n, par, st);
+            note_launch();
+            k_hook<<<grid_for(m - m1, 256), 256, 0, s>>>(edges, m1, m, n, par, is_tree, st);
+            note_launch();
+        }
     }
     {
         PhaseTimer pt("br.compress", s);
@@ -326,15 +351,20 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
         note_launch();
         rc = last_launch();
     }
-    SortResult sr{};
-    if (!rc) rc = radix_sort_pairs(tuv, nullptr, n_arcs, A > 0 ? A : 1, ceil_log2(uint64_t(n)), n, ws, &sr);
+    if (!rc) {
+        PhaseTimer pt("br.group", s);
+        k_arc_count<<<gA, 256, 0, s>>>(tuv, n_arcs, deg);
+        note_launch();
+        rc = last_launch();
+    }
+    if (!rc) rc = scan_exclusive_i32(deg, off, n, ws);
     if (!rc) {
         PhaseTimer pt("br.forest_succ", s);
-        k_group_bounds<<<gA, 256, 0, s>>>(sr.keys, sr.d_total, first_pos, end_pos);
+        k_arc_scatter<<<gA, 256, 0, s>>>(tuv, n_arcs, off, deg, B);
         note_launch();
-        k_forest_succ<<<gA, 256, 0, s>>>(sr.keys, sr.vals, sr.d_total, N, first_pos, end_pos, succ);
+        k_forest_succ<<<gA, 256, 0, s>>>(B, n_arcs, N, off, succ);
         note_launch();
-        k_root_flags<<<gn, 256, 0, s>>>(n, par, first_pos, rflag);
+        k_root_flags<<<gn, 256, 0, s>>>(n, par, off, rflag);
         note_launch();
         rc = last_launch();
     }
@@ -343,7 +373,7 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
         PhaseTimer pt("br.chain", s);
         k_root_list<<<gn, 256, 0, s>>>(n, rflag, rpos, roots);
         note_launch();
-        k_chain<<<gn, 256, 0, s>>>(n, rpos, roots, sr.vals, first_pos, end_pos, int32_t(A), succ);
+        k_chain<<<gn, 256, 0, s>>>(n, rpos, roots, B, off, int32_t(A), succ);
         note_launch();
         rc = last_launch();
     }
@@ -355,7 +385,7 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
         PhaseTimer pt("br.lowhigh_prep", s);
         k_forest_tin<<<gt, 256, 0, s>>>(rr, n_arcs, tuv, tin, child, etin, etout);
         note_launch();
-        k_root_tin<<<gn, 256, 0, s>>>(n, rpos, roots, sr.vals, first_pos, rr, tin);
+        k_root_tin<<<gn, 256, 0, s>>>(n, rpos, roots, B, off, rr, tin);
         note_launch();
         k_nlo_init<<<gn, 256, 0, s>>>(n, tin, nlo, nhi);
         note_launch();

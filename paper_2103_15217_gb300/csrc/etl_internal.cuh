@@ -107,12 +107,11 @@ etl_status scan_exclusive_u8(const uint8_t *in, int32_t *out, int64_t n, Workspa
 // with key_limit <= 2^key_bits. Elements are in[0..count) where count =
 // *d_count if d_count != null else n_cap. With vals_in == null the value of
 // element i is i. Elements whose key is outside [0, key_limit) are dropped
-// (they do not appear in the output). On return
-// *keys_out / *vals_out point at the sorted arrays (inside the workspace) and
-// *d_total (device) holds the number of elements kept.
+// (they do not appear in the output). On return kv points at the sorted
+// (key, value) pairs (inside the workspace) and *d_total (device) holds the
+// number of elements kept.
 struct SortResult {
-    const int32_t *keys;
-    const int32_t *vals;
+    const int2 *kv;
     const int32_t *d_total;
 };
 etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, const int32_t *d_count, int64_t n_cap,

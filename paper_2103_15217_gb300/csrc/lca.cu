@@ -22,7 +22,9 @@
 //      prefix sum of Sec. 2); size = (rank(2v+1) - rank(2v) + 1) / 2. In a
 //      chained batch, tree i occupies preorder positions node_off[i] ..
 //      node_off[i+1]-1 and depth / size come out per tree.
-//   6. k_parent_pre: Q[pre(v)] = pre(parent(v)), level 0 of the sparse table.
+//   6. k_parent_pre: Q[pre(v)] = pre(parent(v)), level 0 of the sparse table
+//      (a separate pass: gathering pre[] is cheaper than re-deriving the
+//      parent's preorder from its bracket record).
 //   7. sparse table over Q (rmq.cu), as many levels as the largest tree needs.
 //
 // Query: for u != v with i = min(pre u, pre v), j = max(...), every node with
@@ -107,17 +109,19 @@ __global__ void k_check_roots(const int32_t *__restrict__ root_cnt, const int32_
     if (gtid() == 0) *head = 2 * root_of[0];
 }
 
-__global__ void k_tour_succ(const int32_t *__restrict__ keys, const int32_t *__restrict__ kids,
-                            const int32_t *__restrict__ coff, int32_t n, int32_t *__restrict__ succ) {
+// kv[t] = (parent, child), grouped by parent with children ascending
+__global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restrict__ coff, int32_t n,
+                            int32_t *__restrict__ succ) {
     const int32_t kept = coff[n];  // number of (parent, child) pairs
     for (int64_t t = gtid(); t < n; t += gstride()) {
         const int32_t v = int32_t(t);
         const int32_t b = coff[v], e = coff[v + 1];
-        succ[2 * v] = (b < e) ? 2 * kids[b] : 2 * v + 1;  // enter v -> enter first child, or leave v
+        succ[2 * v] = (b < e) ? 2 * kv[b].y : 2 * v + 1;  // enter v -> enter first child, or leave v
         if (t < kept) {                                    // position t of the grouped children
-            const int32_t c = kids[t], p = keys[t];
+            const int2 pc = kv[t];
+            const int32_t c = pc.y, p = pc.x;
             if (c >= 0 && c < n && p >= 0 && p < n) {
-                const int32_t sib = (t + 1 < coff[p + 1]) ? kids[t + 1] : -1;
+                const int32_t sib = (t + 1 < coff[p + 1]) ? kv[t + 1].y : -1;
                 succ[2 * c + 1] = sib >= 0 ? 2 * sib : 2 * p + 1;  // leave c -> enter next sibling, or leave p
             }
         }
@@ -154,6 +158,14 @@ __global__ void k_node_stats(RankResult rr, int32_t n, int32_t *__restrict__ pre
     }
 }
 
+__global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *__restrict__ pre, int32_t n,
+                             int32_t *__restrict__ q0) {
+    for (int64_t v = gtid(); v < n; v += gstride()) {
+        const int32_t i = pre[v], p = parent[v];
+        if (i >= 0 && i < n) q0[i] = (p >= 0 && p < n) ? __ldg(pre + p) : -1;  // root: never inside a range
+    }
+}
+
 // root i must open its tree at preorder off[i] and span the whole instance
 __global__ void k_check_instances(const int32_t *__restrict__ root_of, const int32_t *__restrict__ off, int32_t k,
                                   int32_t n, const int32_t *__restrict__ pre, const int32_t *__restrict__ size,
@@ -162,14 +174,6 @@ __global__ void k_check_instances(const int32_t *__restrict__ root_of, const int
         const int32_t b = off ? off[i] : 0, e = off ? off[i + 1] : n;
         const int32_t r = root_of[i];
         if (r < 0 || r >= n || pre[r] != b || size[r] != e - b) set_status(status, ETL_EBADTREE);
-    }
-}
-
-__global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *__restrict__ pre, int32_t n,
-                             int32_t *__restrict__ q0) {
-    for (int64_t v = gtid(); v < n; v += gstride()) {
-        const int32_t i = pre[v], p = parent[v];
-        if (i >= 0 && i < n) q0[i] = (p >= 0 && p < n) ? __ldg(pre + p) : -1;
     }
 }
 
@@ -325,7 +329,7 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
         if (!st) st = radix_sort_pairs(par, nullptr, nullptr, n, ceil_log2(uint64_t(n)), n, ws, &sr);
         if (!st) {
             PhaseTimer pt("lca.succ", s);
-            k_tour_succ<<<grid_for(n, 256), 256, 0, s>>>(sr.keys, sr.vals, coff, n, succ);
+            k_tour_succ<<<grid_for(n, 256), 256, 0, s>>>(sr.kv, coff, n, succ);
             note_launch();
             k_link_roots<<<grid_for(k, 256), 256, 0, s>>>(root_of, k, n, succ);
             note_launch();

@@ -80,6 +80,8 @@ RmqParams &rmq_params() {
     return p;
 }
 
+constexpr int64_t kL2ReuseBytes = int64_t(48) << 20;  // share of the 129 MB L2 one sweep may rely on
+
 int64_t sparse_ld(int64_t n) { return (n + 3) & ~int64_t(3); }
 
 int sparse_levels(int64_t max_len) {
@@ -98,7 +100,12 @@ etl_status sparse_table_build(int32_t *table, int64_t n, int levels, cudaStream_
     const RmqParams &R = rmq_params();
     const int grid_cap = num_sms() * (2048 / R.block);
     for (int l = 1; l < levels;) {
-        const int count = levels - l >= R.levels_per_pass ? R.levels_per_pass : levels - l;
+        // fuse c levels only while the 2^c shifted streams stay inside L2: a pass re-reads each
+        // entry of level l-1 at offsets up to (2^c - 1) * 2^(l-1), so the reuse window spans
+        // about 2^c * (2^c - 1) * 2^(l-1) * 4 bytes of the sweep
+        int count = levels - l >= R.levels_per_pass ? R.levels_per_pass : levels - l;
+        const int64_t h = int64_t(1) << (l - 1);
+        while (count > 1 && (int64_t(1) << count) * ((int64_t(1) << count) - 1) * h * 4 > kL2ReuseBytes) --count;
         int blocks = int(ceil_div(ld / 4, R.block));
         if (blocks > grid_cap) blocks = grid_cap;
         if (blocks < 1) blocks = 1;

@@ -28,20 +28,29 @@ __device__ __forceinline__ int64_t count_of(const int32_t *d_count, int64_t n_ca
     return c < 0 ? 0 : (c < n_cap ? c : n_cap);
 }
 
+// keys of the input: a plain array (first pass) or the .x of (key, value) pairs (later passes)
+__device__ __forceinline__ int32_t key_at(const int32_t *keys, const int2 *kv, int64_t i) {
+    return kv ? kv[i].x : keys[i];
+}
+
 __global__ void __launch_bounds__(kThreads)
-    k_hist(const int32_t *__restrict__ keys, const int32_t *d_count, int64_t n_cap, int shift, int32_t key_limit,
-           int32_t *__restrict__ ghist, int nblocks) {
+    k_hist(const int32_t *__restrict__ keys, const int2 *__restrict__ kv, const int32_t *d_count, int64_t n_cap,
+           int shift, int32_t key_limit, int32_t *__restrict__ ghist, int nblocks) {
     __shared__ int32_t h[kRadix];
+    const int64_t count = count_of(d_count, n_cap);
+    if (int64_t(blockIdx.x) * kTile >= count) {  // tile past the data: an all-zero histogram
+        for (int d = threadIdx.x; d < kRadix; d += kThreads) ghist[int64_t(d) * nblocks + blockIdx.x] = 0;
+        return;
+    }
     for (int d = threadIdx.x; d < kRadix; d += kThreads) h[d] = 0;
     __syncthreads();
-    const int64_t count = count_of(d_count, n_cap);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kTile + warp * kWarpTile;
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         int64_t idx = base + r * kWarp + lane;
         if (idx < count) {
-            int32_t k = keys[idx];
+            int32_t k = key_at(keys, kv, idx);
             if (k >= 0 && k < key_limit) atomicAdd(&h[(k >> shift) & (kRadix - 1)], 1);
         }
     }
@@ -50,14 +59,15 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 __global__ void __launch_bounds__(kThreads)
-    k_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, const int32_t *d_count,
-              int64_t n_cap, int shift, int32_t key_limit, const int32_t *__restrict__ goff, int nblocks,
-              int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
+    k_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, const int2 *__restrict__ kv,
+              const int32_t *d_count, int64_t n_cap, int shift, int32_t key_limit, const int32_t *__restrict__ goff,
+              int nblocks, int2 *__restrict__ kv_out) {
     __shared__ int32_t wcnt[kWarps][kRadix];
     __shared__ int32_t gbase[kRadix];
+    const int64_t count = count_of(d_count, n_cap);
+    if (int64_t(blockIdx.x) * kTile >= count) return;  // nothing of this tile to place
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
-    const int64_t count = count_of(d_count, n_cap);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kTile + warp * kWarpTile;
     int32_t key[kRounds], val[kRounds], dig[kRounds], lrank[kRounds];
@@ -66,8 +76,16 @@ __global__ void __launch_bounds__(kThreads)
         int64_t idx = base + r * kWarp + lane;
         bool valid = false;
         int32_t k = -1;
+        int32_t v = 0;
         if (idx < count) {
-            k = keys[idx];
+            if (kv) {
+                const int2 x = kv[idx];
+                k = x.x;
+                v = x.y;
+            } else {
+                k = keys[idx];
+                v = vals ? vals[idx] : int32_t(idx);
+            }
             valid = (k >= 0 && k < key_limit);
         }
         int d = valid ? ((k >> shift) & (kRadix - 1)) : (kRadix + lane);  // invalid lanes get unique dummies
@@ -78,7 +96,7 @@ __global__ void __launch_bounds__(kThreads)
         if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = pre + __popc(peers);
         __syncwarp();
         key[r] = k;
-        val[r] = valid ? (vals ? vals[idx] : int32_t(idx)) : 0;
+        val[r] = v;
         dig[r] = valid ? d : -1;
         lrank[r] = pre + __popc(peers & lanemask_lt());
     }
@@ -98,8 +116,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int r = 0; r < kRounds; ++r) {
         if (dig[r] >= 0) {
             int32_t dest = gbase[dig[r]] + wcnt[warp][dig[r]] + lrank[r];
-            keys_out[dest] = key[r];
-            vals_out[dest] = val[r];
+            kv_out[dest] = make_int2(key[r], val[r]);
         }
     }
 }
@@ -113,11 +130,11 @@ etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, cons
     const int nblocks = int(ceil_div(cap, kTile));
     const int passes = key_bits <= 8 ? 1 : (key_bits + 7) / 8;
     if (key_bits < 31 && key_limit > (int32_t(1) << key_bits)) key_limit = int32_t(1) << key_bits;
-    int32_t *kbuf[2] = {ws.get<int32_t>(cap), ws.get<int32_t>(cap)};
-    int32_t *vbuf[2] = {ws.get<int32_t>(cap), ws.get<int32_t>(cap)};
+    int2 *buf[2] = {ws.get<int2>(cap), ws.get<int2>(cap)};
     int32_t *ghist = ws.get<int32_t>(int64_t(kRadix) * nblocks);
     if (!ws.ok()) return ETL_ENOMEM;
-    const int32_t *kin = keys_in, *vin = vals_in, *cnt = d_count;
+    const int2 *kvin = nullptr;
+    const int32_t *cnt = d_count;
     for (int p = 0; p < passes; ++p) {
         int32_t *goff = ws.get<int32_t>(int64_t(kRadix) * nblocks + 1);
         if (!ws.ok()) return ETL_ENOMEM;
@@ -125,27 +142,26 @@ etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, cons
         etl_status st;
         {
             PhaseTimer pt("sort.hist", s);
-            k_hist<<<nblocks, kThreads, 0, s>>>(kin, cnt, cap, shift, key_limit, ghist, nblocks);
+            k_hist<<<nblocks, kThreads, 0, s>>>(keys_in, kvin, cnt, cap, shift, key_limit, ghist, nblocks);
         note_launch();
             st = last_launch();
         }
         if (st) return st;
         st = scan_exclusive_i32(ghist, goff, int64_t(kRadix) * nblocks, ws);
         if (st) return st;
-        int32_t *ko = kbuf[p & 1], *vo = vbuf[p & 1];
+        int2 *out_kv = buf[p & 1];
         {
             PhaseTimer pt("sort.scatter", s);
-            k_scatter<<<nblocks, kThreads, 0, s>>>(kin, vin, cnt, cap, shift, key_limit, goff, nblocks, ko, vo);
+            k_scatter<<<nblocks, kThreads, 0, s>>>(keys_in, vals_in, kvin, cnt, cap, shift, key_limit, goff, nblocks,
+                                                   out_kv);
         note_launch();
             st = last_launch();
         }
         if (st) return st;
-        kin = ko;
-        vin = vo;
+        kvin = out_kv;
         cnt = goff + int64_t(kRadix) * nblocks;  // number of kept elements
     }
-    out->keys = kin;
-    out->vals = vin;
+    out->kv = kvin;
     out->d_total = cnt;
     return ETL_OK;
 }

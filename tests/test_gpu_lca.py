@@ -166,3 +166,26 @@ def test_queries_on_other_stream_after_event():
     s.synchronize()
     assert (out.cpu().numpy() == oracle.lca_offline(parent, u, v)).all()
     h.free()
+
+
+@pytest.mark.parametrize("hub", [2, 63, 64, 65, 200, 5000])
+def test_child_group_sizes(hub):
+    # one node with `hub` children inside a random tree: exercises both the
+    # in-place ordering of small sibling groups and the sorted fallback
+    rng = np.random.default_rng(hub)
+    n = 20000
+    parent = synth.tree_parent(n, None, seed=hub)
+    kids = rng.choice(np.nonzero(parent >= 0)[0], size=hub, replace=False)
+    root = int(np.nonzero(parent == -1)[0][0])
+    h_node = int(rng.choice(np.setdiff1d(np.arange(n), np.concatenate([kids, [root]]))))
+    # re-hang the chosen nodes under h_node unless that would create a cycle (h_node below one of them)
+    anc = set()
+    x = h_node
+    while x != -1:
+        anc.add(x)
+        x = int(parent[x])
+    for c in kids:
+        if int(c) not in anc:
+            parent[c] = h_node
+    u, v = synth.lca_queries(n, 3 * n, seed=hub)
+    check_tree(parent, u, v)
