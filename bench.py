@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--small", action="store_true", help="small sizes (functional check only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["all", "core", "batched", "serve"], default="all",
+    ap.add_argument("--mode", choices=["all", "core", "batched", "serve", "methods"], default="all",
                     help="core = the scale workload; batched = 4096 mixed instances, batched vs per-instance")
     ap.add_argument("--case", choices=["lca", "easy", "hard"], default=None,
                     help="run one workload of size --n twice (warm-up + one more) and exit; for profilers")
@@ -323,6 +323,9 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, etl, trees, graphs, dev, units, world)
 
+    methods_res = run_methods(args, dev, trees) if args.mode == "all" else None
+    if args.mode == "methods":
+        methods_res = {"depth_sweep_n_2^23": run_methods(args, dev)}
     batched_res = run_batched(args, dev) if args.mode in ("all", "batched") else None
     serve_res = run_serve(args) if args.mode in ("all", "serve") else None
     result = {
@@ -338,6 +341,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "wall_s_timed": wall},
         "breakdown": breakdown,
+        "lca_methods": methods_res,
         "batched": batched_res,
         "serving": serve_res,
         "e2e": e2e,
@@ -556,6 +560,87 @@ def run_batched(args, dev):
         "speedup": t_pi / t_b, "results_identical": equal, "unit": UNIT,
         "host_launch_sites_during_replay": launches_b,
     }
+
+
+# ------------------------------------------------------------------ LCA methods
+
+def _median_ms(fn, reps=3):
+    import torch
+    s = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def compare_methods(parent_np, u_np, v_np, dev, naive_step_budget=2e9):
+    """RMQ (this path), Inlabel (the paper's GPU method) and naive climbing (the paper's
+    comparison method) on one tree: preprocessing and query times, answers cross-checked."""
+    import torch
+
+    import paper_2103_15217_gb300 as etl
+    n, q = parent_np.shape[0], u_np.shape[0]
+    P = torch.from_numpy(parent_np).to(dev)
+    U, V = torch.from_numpy(u_np).to(dev), torch.from_numpy(v_np).to(dev)
+    res = {"n": n, "q": q}
+    h = etl.lca_preprocess(P)
+    h.build_inlabel(P)
+    torch.cuda.synchronize()
+
+    def pre_rmq():
+        x = etl.lca_preprocess(P)
+        x.free()
+
+    def pre_inl():
+        x = etl.lca_preprocess(P, methods=("inlabel",))
+        x.free()
+    t_rmq_pre = _median_ms(pre_rmq)
+    t_inl_pre = _median_ms(pre_inl)
+    out_r = torch.empty_like(U)
+    out_i = torch.empty_like(U)
+    t_rmq_q = _median_ms(lambda: h.query(U, V, out=out_r))
+    t_inl_q = _median_ms(lambda: h.query_inlabel(U, V, out=out_i))
+    depth_mean = float(h.arrays()["depth"].double().mean().item())
+    # naive: full query set unless its climbs would exceed the step budget; then a prefix sample
+    qn = int(min(q, max(1024, naive_step_budget / max(1.0, 2 * depth_mean))))
+    nv = etl.NaiveLca(P)
+    t_nv_pre = _median_ms(lambda: etl.NaiveLca(P))
+    out_n = torch.empty(qn, dtype=torch.int32, device=dev)
+    t_nv_q = _median_ms(lambda: nv.query(U[:qn], V[:qn], out=out_n), reps=2)
+    agree = bool(torch.equal(out_r, out_i) and torch.equal(out_r[:qn], out_n))
+    h.free()
+    res.update({
+        "avg_depth": depth_mean,
+        "rmq": {"preprocess_ms": t_rmq_pre, "query_ms": t_rmq_q, "queries_per_s": q / t_rmq_q * 1e3},
+        "inlabel": {"preprocess_ms": t_inl_pre, "query_ms": t_inl_q, "queries_per_s": q / t_inl_q * 1e3},
+        "naive": {"preprocess_ms": t_nv_pre, "queries_timed": qn, "query_ms_for_timed": t_nv_q,
+                  "queries_per_s": qn / t_nv_q * 1e3, "query_ms_for_all_q_est": t_nv_q * q / qn},
+        "answers_identical": agree,
+    })
+    return res
+
+
+def run_methods(args, dev, trees=None):
+    """Three n = 2^24 trees of the main workload, or (mode methods) the depth sweep of Sec. 3.3."""
+    import synth
+    out = {}
+    if trees is not None:
+        for t in trees:
+            g = "inf" if t["grasp"] is None else str(t["grasp"])
+            out[f"grasp_{g}"] = compare_methods(t["parent"], t["u"], t["v"], dev)
+        return out
+    n = 1 << 23 if not args.small else 1 << 16
+    for grasp in (None, 100000, 10000, 1000, 100, 10, 1):
+        parent = synth.tree_parent(n, grasp, seed=3)
+        u, v = synth.lca_queries(n, n, seed=3)
+        g = "inf" if grasp is None else str(grasp)
+        out[f"grasp_{g}"] = compare_methods(parent, u, v, dev)
+    return out
 
 
 # ------------------------------------------------------------------ serving

@@ -113,7 +113,18 @@ typedef struct etl_lca_s *etl_lca_t;
 etl_status lca_preprocess(const int32_t *parent, int32_t n, void *stream, etl_lca_t *out);
 
 /*
+ * lca_preprocess_ex: as lca_preprocess, choosing which query structures to
+ * build: ETL_LCA_RMQ (the sparse table, for lca_query) and/or
+ * ETL_LCA_INLABEL (the Inlabel records, for lca_query_inlabel; the paper's
+ * GPU method, O(n) memory). Unknown bits or neither bit: ETL_EINVAL.
+ */
+enum { ETL_LCA_RMQ = 1, ETL_LCA_INLABEL = 2 };
+etl_status lca_preprocess_ex(const int32_t *parent, int32_t n, int32_t flags, void *stream, etl_lca_t *out);
+
+/*
  * lca_query: out[i] = LCA(u[i], v[i]) for i in [0, q), for the tree of h
+ * (built with the RMQ structure: lca_preprocess, or lca_preprocess_ex with
+ * ETL_LCA_RMQ)
  * (Sec. 3, problem statement: the deepest node that is an ancestor of both,
  * a node being its own ancestor). Ids outside [0, n) give out[i] = -1 and
  * ETL_EBADQUERY in *status (device int32, may be NULL; written only on error,
@@ -150,6 +161,36 @@ etl_status lca_preprocess_batch(const int32_t *parent, const int32_t *node_off, 
  * handle) returns ETL_EINVAL.
  */
 etl_status lca_query_batch(etl_lca_t h, const int32_t *inst, const int32_t *u, const int32_t *v, int64_t q,
+                           int32_t *out, int32_t *status, void *stream);
+
+/*
+ * lca_build_inlabel: adds the Inlabel (Schieber-Vishkin) structures to a
+ * single-tree handle -- the paper's GPU LCA method (Sec. 3.1, "The Inlabel
+ * Algorithm") -- from the handle's preorder, size and depth and the same
+ * parent array the handle was built from (device, int32[n]; must still hold
+ * the same values). O(n) extra memory (24 bytes per node). ETL_EINVAL for a
+ * batch handle.
+ * lca_query_inlabel: out[i] = LCA(u[i], v[i]) by the Inlabel method (same
+ * results and error rules as lca_query); needs lca_build_inlabel first.
+ */
+etl_status lca_build_inlabel(etl_lca_t h, const int32_t *parent, void *stream);
+etl_status lca_query_inlabel(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q, int32_t *out,
+                             int32_t *status, void *stream);
+
+/*
+ * The naive GPU LCA the paper compares against (Sec. 3.1, "The Naive
+ * Algorithm"; Martins et al.). lca_naive_preprocess computes every node's
+ * level by pointer jumping (five jumps per global synchronisation) and writes
+ * rec[2v] = parent(v), rec[2v+1] = level(v) (device int32[2n], caller-owned).
+ * lca_naive_query answers each query by climbing: the deeper end up to the
+ * other's level, then both ends together -- O(distance) work per query, so
+ * slow on deep trees (that is the point of the comparison). Parent arrays
+ * that are not one tree give ETL_EBADTREE in *status (device, may be NULL;
+ * preprocessing zeroes it first when given); a climb longer than 2n steps
+ * gives ETL_ETIMEOUT and -1. Same id rules as lca_query.
+ */
+etl_status lca_naive_preprocess(const int32_t *parent, int32_t n, int32_t *rec, int32_t *status, void *stream);
+etl_status lca_naive_query(const int32_t *rec, int32_t n, const int32_t *u, const int32_t *v, int64_t q,
                            int32_t *out, int32_t *status, void *stream);
 
 /*
@@ -237,6 +278,9 @@ etl_status etl_profile_enable(int32_t on);
 etl_status etl_profile_reset(void);
 etl_status etl_profile_count(int32_t *count);
 etl_status etl_profile_get(int32_t i, char *name, int32_t name_len, double *total_ms, int64_t *launches);
+/* Release the device memory the library keeps reserved in its own stream-ordered memory pools
+ * (freed buffers stay reserved for reuse until this call). Synchronous with respect to the pools. */
+etl_status etl_trim(void);
 /* Number of kernels this process has launched through the library so far (host-side counter). */
 etl_status etl_launch_count(int64_t *count);
 

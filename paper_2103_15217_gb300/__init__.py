@@ -26,7 +26,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libetl.so")
 STATUS = {0: "ETL_OK", 1: "ETL_EINVAL", 2: "ETL_ENOMEM", 3: "ETL_ECUDA", 4: "ETL_EBADTREE",
           5: "ETL_EBADQUERY", 6: "ETL_EBADGRAPH", 7: "ETL_ETIMEOUT"}
 EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_preprocess", "lca_query", "lca_status", "lca_arrays",
-           "lca_export", "lca_free", "find_bridges", "lca_preprocess_batch", "lca_query_batch", "find_bridges_batch", "etl_profile_enable", "etl_profile_reset",
+           "lca_export", "lca_free", "find_bridges", "lca_preprocess_batch", "lca_query_batch", "find_bridges_batch",
+           "lca_build_inlabel", "lca_query_inlabel", "lca_naive_preprocess", "lca_naive_query",
+           "lca_preprocess_ex", "etl_trim", "etl_profile_enable", "etl_profile_reset",
            "etl_profile_count", "etl_profile_get", "etl_launch_count", "etl_tune_set", "etl_tune_get")
 TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
              "rmq_levels_per_pass": 5, "rmq_block": 6}
@@ -71,6 +73,12 @@ def load_library(path: str | None = None):
         lib.lca_free.argtypes = [P]
         lib.find_bridges.argtypes = [P, i64, i32, P, P, P]
         lib.lca_preprocess_batch.argtypes = [P, P, i32, i32, i32, P, PP]
+        lib.lca_build_inlabel.argtypes = [P, P, P]
+        lib.lca_preprocess_ex.argtypes = [P, i32, i32, P, PP]
+        lib.etl_trim.argtypes = []
+        lib.lca_naive_preprocess.argtypes = [P, i32, P, P, P]
+        lib.lca_naive_query.argtypes = [P, i32, P, P, i64, P, P, P]
+        lib.lca_query_inlabel.argtypes = [P, P, P, i64, P, P, P]
         lib.lca_query_batch.argtypes = [P, P, P, P, i64, P, P, P]
         lib.find_bridges_batch.argtypes = [P, P, P, i32, i64, i32, P, P, P]
         lib.etl_launch_count.argtypes = [ctypes.POINTER(i64)]
@@ -128,7 +136,7 @@ class Lca:
     """A preprocessed tree, or a batch of trees: wraps an ``etl_lca_t`` handle."""
 
     def __init__(self, parent: torch.Tensor, stream=None, node_off: torch.Tensor | None = None,
-                 max_n: int | None = None):
+                 max_n: int | None = None, methods: tuple = ("rmq",)):
         lib = load_library()
         self._lib = lib
         self.n = parent.numel()
@@ -142,8 +150,9 @@ class Lca:
                 int(max_n if max_n is not None else self.n), self._stream, ctypes.byref(self._h)))
         else:
             self.k = 1
-            _check("lca_preprocess", lib.lca_preprocess(_dev_i32(parent, "parent"), self.n, self._stream,
-                                                        ctypes.byref(self._h)))
+            flags = (1 if "rmq" in methods else 0) | (2 if "inlabel" in methods else 0)
+            _check("lca_preprocess_ex", lib.lca_preprocess_ex(_dev_i32(parent, "parent"), self.n, flags,
+                                                              self._stream, ctypes.byref(self._h)))
         self._refs = (parent, node_off)  # keep the inputs alive until preprocessing has run
 
     def query(self, u: torch.Tensor, v: torch.Tensor, out: torch.Tensor | None = None,
@@ -166,6 +175,24 @@ class Lca:
         _check("lca_query_batch", self._lib.lca_query_batch(self._h, _dev_i32(inst, "inst"), _dev_i32(u, "u"),
                                                             _dev_i32(v, "v"), u.numel(), _dev_i32(out, "out"),
                                                             _status_ptr(status), _stream(stream)))
+        return out
+
+    def build_inlabel(self, parent: torch.Tensor, stream=None):
+        """Add the Inlabel (Schieber-Vishkin) structures; parent = the array the handle was built from."""
+        _check("lca_build_inlabel", self._lib.lca_build_inlabel(self._h, _dev_i32(parent, "parent"), _stream(stream)))
+        self._refs = self._refs + (parent,)
+        return self
+
+    def query_inlabel(self, u: torch.Tensor, v: torch.Tensor, out: torch.Tensor | None = None,
+                      status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """LCA by the Inlabel method (needs build_inlabel)."""
+        if u.numel() != v.numel():
+            raise ValueError("u and v must have the same length")
+        if out is None:
+            out = torch.empty_like(u)
+        _check("lca_query_inlabel", self._lib.lca_query_inlabel(self._h, _dev_i32(u, "u"), _dev_i32(v, "v"), u.numel(),
+                                                                _dev_i32(out, "out"), _status_ptr(status),
+                                                                _stream(stream)))
         return out
 
     def status(self) -> int:
@@ -241,13 +268,40 @@ def profile_read() -> dict:
     return out
 
 
-def lca_preprocess(parent: torch.Tensor, stream=None) -> Lca:
-    return Lca(parent, stream)
+def lca_preprocess(parent: torch.Tensor, stream=None, methods: tuple = ("rmq",)) -> Lca:
+    """Preprocess one tree; methods: any of "rmq" (lca query) and "inlabel" (query_inlabel)."""
+    return Lca(parent, stream, methods=methods)
+
+
+def trim():
+    """Give back the device memory the library keeps reserved for reuse."""
+    _check("etl_trim", load_library().etl_trim())
 
 
 def lca_preprocess_batch(parent: torch.Tensor, node_off: torch.Tensor, max_n: int, stream=None) -> Lca:
     """Trees concatenated in local ids; node_off (device int32[k+1]) delimits them."""
     return Lca(parent, stream, node_off=node_off, max_n=max_n)
+
+
+class NaiveLca:
+    """The paper's naive GPU LCA (levels by pointer jumping, queries by climbing)."""
+
+    def __init__(self, parent: torch.Tensor, status: torch.Tensor | None = None, stream=None):
+        self._lib = load_library()
+        self.n = parent.numel()
+        self.rec = torch.empty(2 * self.n, dtype=torch.int32, device=parent.device)
+        _check("lca_naive_preprocess", self._lib.lca_naive_preprocess(_dev_i32(parent, "parent"), self.n,
+                                                                      self.rec.data_ptr(), _status_ptr(status),
+                                                                      _stream(stream)))
+
+    def query(self, u: torch.Tensor, v: torch.Tensor, out: torch.Tensor | None = None,
+              status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty_like(u)
+        _check("lca_naive_query", self._lib.lca_naive_query(self.rec.data_ptr(), self.n, _dev_i32(u, "u"),
+                                                            _dev_i32(v, "v"), u.numel(), _dev_i32(out, "out"),
+                                                            _status_ptr(status), _stream(stream)))
+        return out
 
 
 def find_bridges_batch(edges: torch.Tensor, edge_off: torch.Tensor, node_off: torch.Tensor, total_n: int,

@@ -20,9 +20,46 @@ int num_sms() {
     return cached[dev];
 }
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {nullptr};
+}  // namespace
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return cudaMallocAsync(p, bytes, s);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> g(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t np = nullptr;
+            if (cudaMemPoolCreate(&np, &props) != cudaSuccess) return cudaMallocAsync(p, bytes, s);
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            g_pool[dev] = np;
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 }  // namespace etl
 
 using namespace etl;
+
+extern "C" etl_status etl_trim(void) {
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    for (cudaMemPool_t p : g_pool)
+        if (p && cudaMemPoolTrimTo(p, 0) != cudaSuccess) return ETL_ECUDA;
+    return ETL_OK;
+}
 
 extern "C" const char *etl_status_string(int32_t status) {
     switch (status) {

@@ -20,6 +20,13 @@ constexpr unsigned kFull = 0xffffffffu;
 // Number of SMs of the current device (cached per device).
 int num_sms();
 
+// Stream-ordered device allocation from the library's own per-device memory
+// pool, which keeps freed memory reserved (release threshold = max) so that
+// repeated calls do not pay for re-mapping; while the stream is being
+// captured into a graph the default pool is used (graph memory nodes).
+// Freed with cudaFreeAsync. Returns cudaSuccess or the allocator's error.
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
+
 // Stream-ordered scratch: every buffer taken here is released with
 // cudaFreeAsync on the same stream when the Workspace goes out of scope.
 class Workspace {
@@ -33,7 +40,7 @@ class Workspace {
         void *p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
-        if (cudaMallocAsync(&p, bytes, s_) != cudaSuccess) {
+        if (dev_alloc(&p, bytes, s_) != cudaSuccess) {
             ok_ = false;
             return nullptr;
         }
@@ -196,4 +203,7 @@ struct etl_lca_s {
     int64_t ld = 0;             // row length of the sparse table
     int32_t *table = nullptr;   // levels * ld
     int32_t *status = nullptr;  // device status word
+    bool has_table = false;     // RMQ sparse table built (lca_query available)
+    void *inrec = nullptr;      // Inlabel: per node (inlabel, ascendant, depth, parent), int4[n]
+    void *inpath = nullptr;     // Inlabel: per inlabel value (parent of the path head, its depth), int2[n+1]
 };

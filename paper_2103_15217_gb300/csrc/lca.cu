@@ -260,29 +260,33 @@ void free_handle(etl_lca_s *h) {
     cudaStream_t s = h->stream;
     for (int32_t *p : {h->pre, h->depth, h->size, h->order, h->table, h->status, h->node_off})
         if (p) cudaFreeAsync(p, s);
+    for (void *p : {h->inrec, h->inpath})
+        if (p) cudaFreeAsync(p, s);
     delete h;
 }
 
 // n nodes in k >= 1 trees; node_off (device, k+1 entries) is null for one tree
 etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, int32_t k, int32_t max_n,
-                     cudaStream_t s, etl_lca_t *out) {
+                     bool with_table, cudaStream_t s, etl_lca_t *out) {
     const bool batch = node_off != nullptr;
     etl_lca_s *h = new etl_lca_s;
     h->n = n;
     h->k = k;
     h->stream = s;
     h->levels = max_n > 1 ? sparse_levels(max_n - 1) : 1;
+    h->has_table = with_table;
     h->ld = sparse_ld(n);
     const size_t nb = size_t(n) * sizeof(int32_t);
-    bool ok = cudaMallocAsync((void **)&h->pre, nb, s) == cudaSuccess;
-    ok = ok && cudaMallocAsync((void **)&h->depth, nb, s) == cudaSuccess;
-    ok = ok && cudaMallocAsync((void **)&h->size, nb, s) == cudaSuccess;
-    ok = ok && cudaMallocAsync((void **)&h->order, nb, s) == cudaSuccess;
-    ok = ok && cudaMallocAsync((void **)&h->table, size_t(h->ld) * sizeof(int32_t) * size_t(h->levels), s) ==
-                   cudaSuccess;
-    ok = ok && cudaMallocAsync((void **)&h->status, sizeof(int32_t), s) == cudaSuccess;
+    bool ok = dev_alloc((void **)&h->pre, nb, s) == cudaSuccess;
+    ok = ok && dev_alloc((void **)&h->depth, nb, s) == cudaSuccess;
+    ok = ok && dev_alloc((void **)&h->size, nb, s) == cudaSuccess;
+    ok = ok && dev_alloc((void **)&h->order, nb, s) == cudaSuccess;
+    if (with_table)
+        ok = ok && dev_alloc((void **)&h->table, size_t(h->ld) * sizeof(int32_t) * size_t(h->levels), s) ==
+                       cudaSuccess;
+    ok = ok && dev_alloc((void **)&h->status, sizeof(int32_t), s) == cudaSuccess;
     if (ok && batch)
-        ok = cudaMallocAsync((void **)&h->node_off, size_t(k + 1) * sizeof(int32_t), s) == cudaSuccess;
+        ok = dev_alloc((void **)&h->node_off, size_t(k + 1) * sizeof(int32_t), s) == cudaSuccess;
     if (!ok) {
         free_handle(h);
         return ETL_ENOMEM;
@@ -346,13 +350,13 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
             note_launch();
             st = last_launch();
         }
-        if (!st) {
+        if (!st && with_table) {
             PhaseTimer pt("lca.parent_pre", s);
             k_parent_pre<<<grid_for(n, 256), 256, 0, s>>>(par, h->pre, n, h->table);
             note_launch();
             st = last_launch();
         }
-        if (!st) st = sparse_table_build<false>(h->table, n, h->levels, s);
+        if (!st && with_table) st = sparse_table_build<false>(h->table, n, h->levels, s);
     }
     if (st) {
         free_handle(h);
@@ -384,7 +388,28 @@ extern "C" etl_status lca_preprocess(const int32_t *parent, int32_t n, void *str
     if (!out) return ETL_EINVAL;
     *out = nullptr;
     if (!parent || n < 1 || n > (1 << 30)) return ETL_EINVAL;
-    return lca_build(parent, n, nullptr, 1, n, static_cast<cudaStream_t>(stream), out);
+    return lca_build(parent, n, nullptr, 1, n, true, static_cast<cudaStream_t>(stream), out);
+}
+
+etl_status lca_build_inlabel_impl(etl_lca_t h, const int32_t *parent, cudaStream_t s);
+
+extern "C" etl_status lca_preprocess_ex(const int32_t *parent, int32_t n, int32_t flags, void *stream,
+                                        etl_lca_t *out) {
+    if (!out) return ETL_EINVAL;
+    *out = nullptr;
+    if (!parent || n < 1 || n > (1 << 30) || !(flags & (ETL_LCA_RMQ | ETL_LCA_INLABEL)) ||
+        (flags & ~(ETL_LCA_RMQ | ETL_LCA_INLABEL)))
+        return ETL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    etl_status st = lca_build(parent, n, nullptr, 1, n, (flags & ETL_LCA_RMQ) != 0, s, out);
+    if (!st && (flags & ETL_LCA_INLABEL)) {
+        st = lca_build_inlabel_impl(*out, parent, s);
+        if (st) {
+            free_handle(*out);
+            *out = nullptr;
+        }
+    }
+    return st;
 }
 
 extern "C" etl_status lca_preprocess_batch(const int32_t *parent, const int32_t *node_off, int32_t k,
@@ -393,12 +418,12 @@ extern "C" etl_status lca_preprocess_batch(const int32_t *parent, const int32_t 
     *out = nullptr;
     if (!parent || !node_off || k < 1 || total_n < k || total_n > (1 << 30) || max_n < 1 || max_n > total_n)
         return ETL_EINVAL;
-    return lca_build(parent, total_n, node_off, k, max_n, static_cast<cudaStream_t>(stream), out);
+    return lca_build(parent, total_n, node_off, k, max_n, true, static_cast<cudaStream_t>(stream), out);
 }
 
 extern "C" etl_status lca_query(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q, int32_t *out,
                                 int32_t *status, void *stream) {
-    if (!h || h->node_off || q < 0 || q > (int64_t(1) << 40)) return ETL_EINVAL;
+    if (!h || h->node_off || !h->has_table || q < 0 || q > (int64_t(1) << 40)) return ETL_EINVAL;
     if (q == 0) return ETL_OK;
     if (!u || !v || !out) return ETL_EINVAL;
     return query_launch(h, nullptr, u, v, q, out, status, static_cast<cudaStream_t>(stream));
