@@ -625,6 +625,22 @@ def compare_methods(parent_np, u_np, v_np, dev, naive_step_budget=2e9):
     return res
 
 
+def compare_bridge_methods(edges_np, n, dev):
+    """Tarjan-Vishkin (this path) against the paper's hybrid (tour levels + CK marking)."""
+    import torch
+
+    import paper_2103_15217_gb300 as etl
+    E = torch.from_numpy(edges_np).to(dev)
+    a = etl.find_bridges(E, n)
+    b = etl.find_bridges(E, n, method="hybrid")
+    torch.cuda.synchronize()
+    t_tv = _median_ms(lambda: etl.find_bridges(E, n))
+    t_hy = _median_ms(lambda: etl.find_bridges(E, n, method="hybrid"))
+    m = edges_np.shape[0]
+    return {"n": n, "m": m, "tv_ms": t_tv, "hybrid_ms": t_hy, "tv_edges_per_s": m / t_tv * 1e3,
+            "hybrid_edges_per_s": m / t_hy * 1e3, "masks_identical": bool(torch.equal(a, b))}
+
+
 def run_methods(args, dev, trees=None):
     """Three n = 2^24 trees of the main workload, or (mode methods) the depth sweep of Sec. 3.3."""
     import synth
@@ -634,6 +650,11 @@ def run_methods(args, dev, trees=None):
             g = "inf" if t["grasp"] is None else str(t["grasp"])
             out[f"grasp_{g}"] = compare_methods(t["parent"], t["u"], t["v"], dev)
         return out
+    for kind, n in (("easy", 1 << 20), ("hard", 1 << 20), ("easy", 1 << 22), ("hard", 1 << 22)):
+        if args.small:
+            n = 1 << 14
+        e = synth.easy_graph(n, 8 * n, seed=5) if kind == "easy" else synth.hard_graph(n, 4 * n, n // 64, seed=5)
+        out[f"bridges_{kind}_n{n}"] = compare_bridge_methods(e, n, dev)
     n = 1 << 23 if not args.small else 1 << 16
     for grasp in (None, 100000, 10000, 1000, 100, 10, 1):
         parent = synth.tree_parent(n, grasp, seed=3)

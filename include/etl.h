@@ -298,6 +298,28 @@ etl_status etl_launch_count(int64_t *count);
 etl_status find_bridges_batch(const int32_t *edges, const int32_t *edge_off, const int32_t *node_off, int32_t k,
                               int64_t total_m, int32_t total_n, uint8_t *is_bridge, int32_t *status, void *stream);
 
+/*
+ * find_bridges_hybrid: the hybrid the paper proposes (Sec. 4.3): the same
+ * connected-components spanning forest and Euler tour as find_bridges, used
+ * only for parents and levels, followed by Chaitanya-Kothapalli marking --
+ * every non-tree edge walks both ends up to their LCA and marks the tree
+ * edges it passes; tree edges left unmarked are bridges. Same results and
+ * rules as find_bridges; work grows with the tree distance between the ends
+ * of each non-tree edge (a walk longer than 2n steps sets ETL_ETIMEOUT).
+ */
+etl_status find_bridges_hybrid(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
+                               void *stream);
+
+/*
+ * two_edge_cc: 2-edge-connected components, by the decomposition Sec. 4
+ * describes: find all bridges (find_bridges), delete them, and take the
+ * connected components of the rest (the same hook-and-compress pass).
+ * label[v] (device int32[n]) = the smallest vertex of v's component.
+ * Same input rules as find_bridges; on a data error every label is -1 and
+ * *status (device, may be NULL; zeroed first) holds the code.
+ */
+etl_status two_edge_cc(const int32_t *edges, int64_t m, int32_t n, int32_t *label, int32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

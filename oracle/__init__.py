@@ -55,8 +55,9 @@ def bind(lib):
     lib.oracle_lca_offline.argtypes = [i32, P, i64, P, P, P]
     lib.oracle_bridges_dfs.argtypes = [i32, i64, P, P]
     lib.oracle_bridges_tv.argtypes = [i32, i64, P, P, P]
+    lib.oracle_two_edge_cc.argtypes = [i32, i64, P, P]
     for f in ("oracle_tree_tour", "oracle_dcel_tour", "oracle_lca_climb", "oracle_lca_offline",
-              "oracle_bridges_dfs", "oracle_bridges_tv"):
+              "oracle_bridges_dfs", "oracle_bridges_tv", "oracle_two_edge_cc"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -139,4 +140,12 @@ def bridges_tv(n, edges, tree=None):
     t = None if tree is None else np.ascontiguousarray(tree, dtype=np.uint8)
     out = np.empty(edges.shape[0], np.uint8)
     _check("oracle_bridges_tv", _load().oracle_bridges_tv(int(n), edges.shape[0], _p(edges), _p(t), _p(out)))
+    return out
+
+
+def two_edge_cc(n, edges):
+    """Label of every vertex's 2-edge-connected component (its smallest vertex)."""
+    edges = _i32(edges).reshape(-1, 2)
+    out = np.empty(int(n), np.int32)
+    _check("oracle_two_edge_cc", _load().oracle_two_edge_cc(int(n), edges.shape[0], _p(edges), _p(out)))
     return out

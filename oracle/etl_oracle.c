@@ -20,6 +20,8 @@
  *                        function: bridge iff low(u) >= pre(u) (Sec. 4.1).
  *   oracle_bridges_tv    Tarjan-Vishkin criterion with an arbitrary spanning
  *                        forest: low and high over each subtree (Sec. 4.1).
+ *   oracle_two_edge_cc   2-edge-connected components: delete the bridges,
+ *                        take connected components (Sec. 4).
  *
  * Conventions: parent[root] = -1; node ids in [0, n); arcs of a rooted tree are
  * numbered 2v (the arc entering v from its parent, "down", an opening bracket)
@@ -457,4 +459,29 @@ out:
     free(intree); free(uf); free(sz); free(tedges); free(tid); free(off); free(nbr); free(eid); free(pre);
     free(size); free(nlo); free(nhi); free(in_edge); free(cursor); free(stack);
     return rc;
+}
+
+/*
+ * 2-edge-connected components (Sec. 4, the decomposition the paper describes:
+ * find all bridges, delete them, take connected components of what is left).
+ * label[v] = the smallest vertex of v's component. Bridges from the DFS
+ * method above; components by union-find over the remaining edges.
+ */
+int oracle_two_edge_cc(int32_t n, int64_t m, const int32_t *edges, int32_t *label) {
+    if (n < 1 || m < 0 || !label || (m > 0 && !edges)) return OR_EINVAL;
+    uint8_t *br = (uint8_t *)malloc((size_t)(m + 1));
+    int32_t *uf = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!br || !uf) { free(br); free(uf); return OR_ENOMEM; }
+    int rc = m > 0 ? oracle_bridges_dfs(n, m, edges, br) : OR_OK;
+    if (rc) { free(br); free(uf); return rc; }
+    for (int32_t x = 0; x < n; ++x) uf[x] = x;
+    for (int64_t e = 0; e < m; ++e) {
+        if (br[e]) continue;
+        int32_t a = uf_find(uf, edges[2 * e]), b = uf_find(uf, edges[2 * e + 1]);
+        if (a == b) continue;
+        if (a < b) uf[b] = a; else uf[a] = b;  /* the smaller vertex stays the representative */
+    }
+    for (int32_t x = 0; x < n; ++x) label[x] = uf_find(uf, x);
+    free(br); free(uf);
+    return OR_OK;
 }

@@ -28,7 +28,7 @@ STATUS = {0: "ETL_OK", 1: "ETL_EINVAL", 2: "ETL_ENOMEM", 3: "ETL_ECUDA", 4: "ETL
 EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_preprocess", "lca_query", "lca_status", "lca_arrays",
            "lca_export", "lca_free", "find_bridges", "lca_preprocess_batch", "lca_query_batch", "find_bridges_batch",
            "lca_build_inlabel", "lca_query_inlabel", "lca_naive_preprocess", "lca_naive_query",
-           "lca_preprocess_ex", "etl_trim", "etl_profile_enable", "etl_profile_reset",
+           "lca_preprocess_ex", "etl_trim", "two_edge_cc", "find_bridges_hybrid", "etl_profile_enable", "etl_profile_reset",
            "etl_profile_count", "etl_profile_get", "etl_launch_count", "etl_tune_set", "etl_tune_get")
 TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
              "rmq_levels_per_pass": 5, "rmq_block": 6}
@@ -75,6 +75,8 @@ def load_library(path: str | None = None):
         lib.lca_preprocess_batch.argtypes = [P, P, i32, i32, i32, P, PP]
         lib.lca_build_inlabel.argtypes = [P, P, P]
         lib.lca_preprocess_ex.argtypes = [P, i32, i32, P, PP]
+        lib.two_edge_cc.argtypes = [P, i64, i32, P, P, P]
+        lib.find_bridges_hybrid.argtypes = [P, i64, i32, P, P, P]
         lib.etl_trim.argtypes = []
         lib.lca_naive_preprocess.argtypes = [P, i32, P, P, P]
         lib.lca_naive_query.argtypes = [P, i32, P, P, i64, P, P, P]
@@ -320,13 +322,27 @@ def find_bridges_batch(edges: torch.Tensor, edge_off: torch.Tensor, node_off: to
     return mask
 
 
-def find_bridges(edges: torch.Tensor, n: int, status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """uint8 mask, 1 for every bridge of the undirected multigraph (m, 2)."""
+def find_bridges(edges: torch.Tensor, n: int, status: torch.Tensor | None = None, stream=None,
+                 method: str = "tv") -> torch.Tensor:
+    """uint8 mask, 1 for every bridge of the undirected multigraph (m, 2).
+    method: "tv" (Tarjan-Vishkin low/high) or "hybrid" (tour levels + Chaitanya-Kothapalli marking)."""
     lib = load_library()
     if edges.dim() != 2 or edges.shape[1] != 2:
         raise ValueError("edges must have shape (m, 2)")
     m = edges.shape[0]
     mask = torch.empty(m, dtype=torch.uint8, device=edges.device)
-    _check("find_bridges", lib.find_bridges(_dev_i32(edges, "edges"), m, int(n), mask.data_ptr(),
-                                            _status_ptr(status), _stream(stream)))
+    fn = {"tv": lib.find_bridges, "hybrid": lib.find_bridges_hybrid}[method]
+    _check("find_bridges", fn(_dev_i32(edges, "edges"), m, int(n), mask.data_ptr(), _status_ptr(status),
+                              _stream(stream)))
     return mask
+
+
+def two_edge_cc(edges: torch.Tensor, n: int, status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """2-edge-connected component label (smallest vertex) of every vertex."""
+    lib = load_library()
+    if edges.dim() != 2 or edges.shape[1] != 2:
+        raise ValueError("edges must have shape (m, 2)")
+    label = torch.empty(int(n), dtype=torch.int32, device=edges.device)
+    _check("two_edge_cc", lib.two_edge_cc(_dev_i32(edges, "edges"), edges.shape[0], int(n), label.data_ptr(),
+                                          _status_ptr(status), _stream(stream)))
+    return label

@@ -57,12 +57,16 @@ __device__ __forceinline__ int32_t find_root(int32_t *par, int32_t x, int64_t &b
     return -1;
 }
 
+// skip (may be null): edges to leave out; is_tree (may be null): 1 for edges whose hook succeeded
 __global__ void k_hook(const int32_t *__restrict__ edges, int64_t e0, int64_t e1, int32_t n,
-                       int32_t *__restrict__ par, uint8_t *__restrict__ is_tree, int32_t *__restrict__ status) {
+                       int32_t *__restrict__ par, uint8_t *__restrict__ is_tree, const uint8_t *__restrict__ skip,
+                       int32_t *__restrict__ status) {
     for (int64_t e = e0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < e1; e += int64_t(gridDim.x) * blockDim.x) {
         int32_t a = edges[2 * e], b = edges[2 * e + 1];
         uint8_t tree = 0;
-        if (a < 0 || a >= n || b < 0 || b >= n) {
+        if (skip && skip[e]) {
+            // left out
+        } else if (a < 0 || a >= n || b < 0 || b >= n) {
             set_status(status, ETL_EBADGRAPH);
         } else {
             int64_t budget = kFindCap;
@@ -84,7 +88,7 @@ __global__ void k_hook(const int32_t *__restrict__ edges, int64_t e0, int64_t e1
                 b = rb;
             }
         }
-        is_tree[e] = tree;
+        if (is_tree) is_tree[e] = tree;
     }
 }
 
@@ -297,8 +301,109 @@ namespace etl {
 namespace {
 
 // the whole Tarjan-Vishkin pipeline on a graph with global ids; st is a zeroed device status word
+// ---- the hybrid of Sec. 4.3: parents and levels of the rooted forest from its Euler tour, then
+// Chaitanya-Kothapalli marking: every non-tree edge walks both ends up to their LCA and marks the
+// tree edges on the way (a tree edge is named by its child); unmarked tree edges are bridges
+
+__global__ void k_tour_pm(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ etin,
+                          const int32_t *__restrict__ etout, int64_t P, int32_t *__restrict__ val) {
+    const int64_t T = *d_arcs / 2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) val[0] = 0;  // the virtual head
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t a = etin[t], b = etout[t];
+        if (a < 0 || b >= P || a >= b) continue;
+        val[a] = 1;   // down into the child: one level deeper
+        val[b] = -1;  // back up
+    }
+}
+
+__global__ void k_tree_records(int32_t n, const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ tuv,
+                               const int32_t *__restrict__ child, const int32_t *__restrict__ etin,
+                               const int32_t *__restrict__ excl, int64_t P, int2 *__restrict__ trec,
+                               uint8_t *__restrict__ mark) {
+    const int64_t T = *d_arcs / 2;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t c = child[t], a = etin[t];
+        if (a < 0 || a >= P) continue;
+        const int32_t p = tuv[2 * t] == c ? tuv[2 * t + 1] : tuv[2 * t];
+        trec[c] = make_int2(p, excl[a + 1]);  // (parent, level): level = prefix of +-1 at the child's entry
+        mark[c] = 0;
+    }
+}
+
+__global__ void k_tree_records_init(int32_t n, int2 *__restrict__ trec) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        trec[v] = make_int2(-1, 0);  // roots and isolated vertices
+}
+
+__global__ void k_ck_mark(const int32_t *__restrict__ edges, int64_t m, int32_t n, const uint8_t *__restrict__ is_tree,
+                          const int2 *__restrict__ trec, uint8_t *__restrict__ mark, int32_t *__restrict__ status) {
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        if (is_tree[e]) continue;
+        int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        if (a < 0 || a >= n || b < 0 || b >= n || a == b) continue;
+        int2 ra = __ldg(trec + a), rb = __ldg(trec + b);
+        int64_t steps = 0;
+        while (a != b) {
+            if (++steps > 2 * int64_t(n)) {
+                set_status(status, ETL_ETIMEOUT);
+                break;
+            }
+            if (ra.y >= rb.y) {
+                mark[a] = 1;
+                a = ra.x;
+                if (a < 0 || a >= n) break;
+                ra = __ldg(trec + a);
+            } else {
+                mark[b] = 1;
+                b = rb.x;
+                if (b < 0 || b >= n) break;
+                rb = __ldg(trec + b);
+            }
+        }
+    }
+}
+
+__global__ void k_ck_flags(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ child,
+                           const uint8_t *__restrict__ mark, uint8_t *__restrict__ tflag) {
+    const int64_t T = *d_arcs / 2;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x)
+        tflag[t] = mark[child[t]] ? 0 : 1;
+}
+
+etl_status hybrid_marking(const int32_t *edges, int64_t m, int32_t n, const uint8_t *is_tree, const int32_t *tpos,
+                          const int32_t *tuv, const int32_t *n_arcs, const int32_t *child, const int32_t *etin,
+                          const int32_t *etout, int64_t P, uint8_t *tflag, int32_t *st, Workspace &ws) {
+    (void)tpos;
+    cudaStream_t s = ws.stream();
+    int32_t *val = ws.get<int32_t>(P), *excl = ws.get<int32_t>(P + 1);
+    int2 *trec = ws.get<int2>(n);
+    uint8_t *mark = ws.get<uint8_t>(n);
+    if (!ws.ok()) return ETL_ENOMEM;
+    const int gn = grid_for(n, 256);
+    {
+        PhaseTimer pt("hybrid.levels", s);
+        k_tour_pm<<<gn, 256, 0, s>>>(n_arcs, etin, etout, P, val);
+        note_launch();
+    }
+    etl_status rc = last_launch();
+    if (!rc) rc = scan_exclusive_i32(val, excl, P, ws);
+    if (rc) return rc;
+    PhaseTimer pt("hybrid.mark", s);
+    k_tree_records_init<<<gn, 256, 0, s>>>(n, trec);
+    note_launch();
+    k_tree_records<<<gn, 256, 0, s>>>(n, n_arcs, tuv, child, etin, excl, P, trec, mark);
+    note_launch();
+    k_ck_mark<<<grid_for(m, 256), 256, 0, s>>>(edges, m, n, is_tree, trec, mark, st);
+    note_launch();
+    k_ck_flags<<<gn, 256, 0, s>>>(n_arcs, child, mark, tflag);
+    note_launch();
+    return last_launch();
+}
+
+// hybrid: instead of low / high, the Chaitanya-Kothapalli marking on the same rooted forest
 etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *st,
-                        Workspace &ws) {
+                        Workspace &ws, bool hybrid = false) {
     cudaStream_t s = ws.stream();
     const int64_t A = 2 * int64_t(n - 1);  // half-edge capacity of a spanning forest
     const int64_t N = A + 1;                // + the virtual head, at index A
@@ -315,7 +420,8 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     int32_t *succ = ws.get<int32_t>(N);
     int32_t *child = ws.get<int32_t>(n), *etin = ws.get<int32_t>(n), *etout = ws.get<int32_t>(n);
     uint8_t *tflag = ws.get<uint8_t>(n);
-    int32_t *Lt = ws.get<int32_t>(ld * levels), *Ht = ws.get<int32_t>(ld * levels);
+    int32_t *Lt = hybrid ? nullptr : ws.get<int32_t>(ld * levels);
+    int32_t *Ht = hybrid ? nullptr : ws.get<int32_t>(ld * levels);
     if (!ws.ok()) return ETL_ENOMEM;
     etl_status rc = ETL_OK;
     const int gn = grid_for(n, 256), gm = grid_for(m, 256), gA = grid_for(N, 256);
@@ -329,12 +435,12 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
         // after the compression most finds take one step and most edges meet equal roots at once
         const int64_t m1 = m < int64_t(n) ? m : int64_t(n);
         PhaseTimer pt("br.hook", s);
-        k_hook<<<grid_for(m1, 256), 256, 0, s>>>(edges, 0, m1, n, par, is_tree, st);
+        k_hook<<<grid_for(m1, 256), 256, 0, s>>>(edges, 0, m1, n, par, is_tree, nullptr, st);
         note_launch();
         if (m1 < m) {
             k_compress<<<gn, 256, 0, s>>>(n, par, st);
             note_launch();
-            k_hook<<<grid_for(m - m1, 256), 256, 0, s>>>(edges, m1, m, n, par, is_tree, st);
+            k_hook<<<grid_for(m - m1, 256), 256, 0, s>>>(edges, m1, m, n, par, is_tree, nullptr, st);
             note_launch();
         }
     }
@@ -387,6 +493,20 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
         note_launch();
         k_root_tin<<<gn, 256, 0, s>>>(n, rpos, roots, B, off, rr, tin);
         note_launch();
+        rc = last_launch();
+    }
+    if (hybrid) {
+        if (!rc) rc = hybrid_marking(edges, m, n, is_tree, tpos, tuv, n_arcs, child, etin, etout, P, tflag, st, ws);
+        if (!rc) {
+            k_finalize<<<gm, 256, 0, s>>>(m, is_tree, tpos, tflag, st, is_bridge);
+            note_launch();
+            rc = last_launch();
+        }
+        return rc;
+    }
+    if (!rc) {
+        const int gt = grid_for(n, 256);
+        PhaseTimer pt("br.lowhigh_prep", s);
         k_nlo_init<<<gn, 256, 0, s>>>(n, tin, nlo, nhi);
         note_launch();
         k_nontree_minmax<<<gm, 256, 0, s>>>(edges, m, n, is_tree, tin, nlo, nhi);
@@ -406,6 +526,17 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
         rc = last_launch();
     }
     return rc;
+}
+
+__global__ void k_iota(int32_t n, int32_t *__restrict__ x) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        x[v] = int32_t(v);
+}
+
+__global__ void k_labels_on_error(int32_t n, const int32_t *__restrict__ status, int32_t *__restrict__ label) {
+    if (*status == 0) return;
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        label[v] = -1;
 }
 
 // local edge ids of a batch -> global ids: edge e of instance i (edge_off[i] <= e < edge_off[i+1])
@@ -494,4 +625,44 @@ extern "C" etl_status find_bridges_batch(const int32_t *edges, const int32_t *ed
     etl_status rc = last_launch();
     if (rc) return rc;
     return bridges_core(gedges, total_m, total_n, is_bridge, st, ws);
+}
+
+extern "C" etl_status two_edge_cc(const int32_t *edges, int64_t m, int32_t n, int32_t *label, int32_t *status,
+                                  void *stream) {
+    if (n < 1 || n > (1 << 30) || m < 0 || m > int64_t(INT32_MAX) - 1 || !label) return ETL_EINVAL;
+    if (m > 0 && !edges) return ETL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    int32_t *st = status ? status : ws.get<int32_t>(1);
+    uint8_t *is_bridge = ws.get<uint8_t>(m > 0 ? m : 1);
+    if (!ws.ok()) return ETL_ENOMEM;
+    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    etl_status rc = m > 0 ? bridges_core(edges, m, n, is_bridge, st, ws) : ETL_OK;
+    if (rc) return rc;
+    const int gn = grid_for(n, 256);
+    PhaseTimer pt("br.two_edge_cc", s);
+    k_iota<<<gn, 256, 0, s>>>(n, label);
+    note_launch();
+    if (m > 0) {  // connected components of the graph without its bridges; labels = smallest vertex
+        k_hook<<<grid_for(m, 256), 256, 0, s>>>(edges, 0, m, n, label, nullptr, is_bridge, st);
+        note_launch();
+        k_compress<<<gn, 256, 0, s>>>(n, label, st);
+        note_launch();
+    }
+    k_labels_on_error<<<gn, 256, 0, s>>>(n, st, label);
+    note_launch();
+    return last_launch();
+}
+
+extern "C" etl_status find_bridges_hybrid(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge,
+                                          int32_t *status, void *stream) {
+    if (n < 1 || n > (1 << 30) || m < 0 || m > int64_t(INT32_MAX) - 1) return ETL_EINVAL;
+    if (m == 0) return ETL_OK;
+    if (!edges || !is_bridge) return ETL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    int32_t *st = status ? status : ws.get<int32_t>(1);
+    if (!ws.ok()) return ETL_ENOMEM;
+    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    return bridges_core(edges, m, n, is_bridge, st, ws, true);
 }

@@ -81,3 +81,40 @@ def test_config_full_size_easy():
     got, st = gpu_bridges(n, edges)
     assert st == 0
     assert (got == oracle.bridges_dfs(n, edges)).all()
+
+
+def test_two_edge_cc_matches_oracle():
+    import paper_2103_15217_gb300 as etl
+    from oracle import brute
+    rng = np.random.default_rng(31)
+    for trial in range(100):
+        n = int(rng.integers(1, 9))
+        m = int(rng.integers(0, 12))
+        edges = rng.integers(0, n, size=(m, 2)).astype(np.int32)
+        got = host(etl.two_edge_cc(dev(edges.reshape(-1, 2)), n)) if m else host(etl.two_edge_cc(dev(np.zeros((0, 2), np.int32)), n))
+        assert got.tolist() == brute.two_edge_cc(n, edges), (n, edges.tolist())
+    for n, edges in ((1 << 14, synth.easy_graph(1 << 14, 3 << 14, seed=2)),
+                     (1 << 14, synth.hard_graph(1 << 14, 1 << 15, 256, seed=2)),
+                     (1 << 20, synth.hard_graph(1 << 20, 1 << 21, 1 << 14, seed=3))):
+        st = etl.new_status()
+        got = host(etl.two_edge_cc(dev(edges), n, status=st))
+        assert int(host(st)[0]) == 0
+        assert (got == oracle.two_edge_cc(n, edges)).all()
+
+
+def test_hybrid_method_matches_oracle():
+    import paper_2103_15217_gb300 as etl
+    rng = np.random.default_rng(41)
+    for trial in range(150):
+        n = int(rng.integers(1, 12))
+        m = int(rng.integers(1, 18))
+        edges = rng.integers(0, n, size=(m, 2)).astype(np.int32)
+        got = host(etl.find_bridges(dev(edges), n, method="hybrid"))
+        assert got.tolist() == brute.bridges(n, edges), (n, edges.tolist())
+    for n, edges in ((20000, synth.easy_graph(20000, 80000, seed=5)),
+                     (20000, synth.hard_graph(20000, 60000, 300, seed=5)),
+                     (1 << 18, synth.easy_graph(1 << 18, 1 << 21, seed=6))):
+        st = etl.new_status()
+        got = host(etl.find_bridges(dev(edges), n, status=st, method="hybrid"))
+        assert int(host(st)[0]) == 0
+        assert (got == oracle.bridges_dfs(n, edges)).all()

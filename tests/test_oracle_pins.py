@@ -360,3 +360,28 @@ def test_bad_graph_rejected():
         oracle.bridges_dfs(3, np.array([[0, 3]], np.int32))
     with pytest.raises(oracle.OracleError):   # marked edges with a cycle are not a forest
         oracle.bridges_tv(3, np.array([[0, 1], [1, 2], [2, 0]], np.int32), np.ones(3, np.uint8))
+
+
+# --------------------------------------------------------------------------- 2-edge-connected components
+
+
+def test_two_edge_cc_bruteforce():
+    rng = np.random.default_rng(17)
+    for trial in range(300):
+        n = int(rng.integers(1, 9))
+        m = int(rng.integers(0, 12))
+        edges = random_multigraph(rng, n, m)
+        assert oracle.two_edge_cc(n, edges).tolist() == brute.two_edge_cc(n, edges), (n, edges.tolist())
+
+
+def test_two_edge_cc_closed_forms():
+    # a cycle is one component; a tree is all singletons; two cycles joined by a bridge: two components
+    n = 500
+    cyc = np.stack([np.arange(n), (np.arange(n) + 1) % n], 1).astype(np.int32)
+    assert (oracle.two_edge_cc(n, cyc) == 0).all()
+    parent = synth.tree_parent(n, None, seed=2)
+    c = np.nonzero(parent >= 0)[0]
+    assert (oracle.two_edge_cc(n, np.stack([c, parent[c]], 1)) == np.arange(n)).all()
+    two = np.concatenate([cyc[:, :] % 250 + 0, (cyc % 250) + 250, [[3, 400]]]).astype(np.int32)
+    lab = oracle.two_edge_cc(500, two)
+    assert (lab[:250] == 0).all() and (lab[250:] == 250).all()
