@@ -512,6 +512,12 @@ def run_batched(args, dev):
         for i, d in enumerate(B["graphs"]):
             masks_pi[i].copy_(etl.find_bridges(ge[i], d["n"]))
 
+    # launch parameters tuned on a sample of the batch's scale (one tree of up to 2^23 nodes: the
+    # batch is ranked as one chained list of that order of length)
+    from paper_2103_15217_gb300 import tune
+    defaults = etl.tune_get()
+    tuned = tune.autotune(n=int(min(1 << 23, max(1 << 16, int(B["toff"][-1])))), use_cache=False)
+
     def batched():
         h = etl.lca_preprocess_batch(P, O, max_n)
         h.query_batch(I, U, V, out=out_b)
@@ -551,7 +557,10 @@ def run_batched(args, dev):
     g.replay()
     torch.cuda.synchronize()
     equal = equal and bool(torch.equal(torch.cat(outs_pi), out_b) and torch.equal(torch.cat(masks_pi), mask_b))
+    etl.tune_set(**defaults)
     return {
+        "autotuned": {"params": tuned["params"], "sample_ms": tuned["ms"], "default_ms": tuned["default_ms"],
+                      "trials": tuned["trials"]},
         "workload": (f"{len(tp)} trees n log-uniform 2^6..2^18 (grasp 1, 1024, inf round robin) with n queries each"
                      f" + {len(ge)} graphs n log-uniform 2^6..2^16, m = 4n (easy/hard alternating)"),
         "queries": q_total, "edges": m_total, "tree_nodes": int(B["toff"][-1]), "graph_nodes": total_gn,
@@ -655,6 +664,11 @@ def run_methods(args, dev, trees=None):
             n = 1 << 14
         e = synth.easy_graph(n, 8 * n, seed=5) if kind == "easy" else synth.hard_graph(n, 4 * n, n // 64, seed=5)
         out[f"bridges_{kind}_n{n}"] = compare_bridge_methods(e, n, dev)
+    # scale-free trees (Sec. 3.3, "Scale-Free Trees")
+    nb = 1 << 21 if not args.small else 1 << 14
+    parent = synth.ba_tree(nb, seed=3)
+    u, v = synth.lca_queries(nb, nb, seed=3)
+    out[f"barabasi_albert_n{nb}"] = compare_methods(parent, u, v, dev)
     n = 1 << 23 if not args.small else 1 << 16
     for grasp in (None, 100000, 10000, 1000, 100, 10, 1):
         parent = synth.tree_parent(n, grasp, seed=3)

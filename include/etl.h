@@ -253,6 +253,9 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  *                           pass, 1..3 (3)
  *   ETL_TUNE_RMQ_BLOCK      threads per block of the sparse-table build,
  *                           128, 256, 512 or 1024 (256)
+ *   ETL_TUNE_CC_FIRST_SLICE edges hooked before the first compression of the
+ *                           connected-components pass, in units of n/4,
+ *                           1..64 (4, i.e. n edges)
  * Unknown keys or out-of-range values return ETL_EINVAL.
  */
 enum {
@@ -261,7 +264,8 @@ enum {
     ETL_TUNE_RANK_BLOCK = 3,
     ETL_TUNE_RANK_BLOCKS_PER_SM = 4,
     ETL_TUNE_RMQ_LEVELS_PER_PASS = 5,
-    ETL_TUNE_RMQ_BLOCK = 6
+    ETL_TUNE_RMQ_BLOCK = 6,
+    ETL_TUNE_CC_FIRST_SLICE = 7
 };
 etl_status etl_tune_set(int32_t key, int32_t value);
 etl_status etl_tune_get(int32_t key, int32_t *value);

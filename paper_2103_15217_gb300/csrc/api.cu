@@ -118,6 +118,10 @@ extern "C" etl_status etl_tune_set(int32_t key, int32_t value) {
             if (value != 128 && value != 256 && value != 512 && value != 1024) return ETL_EINVAL;
             rmq_params().block = value;
             return ETL_OK;
+        case ETL_TUNE_CC_FIRST_SLICE:
+            if (value < 1 || value > 64) return ETL_EINVAL;
+            cc_params().first_slice_quarters = value;
+            return ETL_OK;
         default:
             return ETL_EINVAL;
     }
@@ -133,6 +137,7 @@ extern "C" etl_status etl_tune_get(int32_t key, int32_t *value) {
         case ETL_TUNE_RANK_BLOCKS_PER_SM: *value = P.blocks_per_sm; return ETL_OK;
         case ETL_TUNE_RMQ_LEVELS_PER_PASS: *value = rmq_params().levels_per_pass; return ETL_OK;
         case ETL_TUNE_RMQ_BLOCK: *value = rmq_params().block; return ETL_OK;
+        case ETL_TUNE_CC_FIRST_SLICE: *value = cc_params().first_slice_quarters; return ETL_OK;
         default: return ETL_EINVAL;
     }
 }

@@ -287,6 +287,15 @@ __global__ void k_finalize(int64_t m, const uint8_t *__restrict__ is_tree, const
         is_bridge[e] = (!bad && is_tree[e]) ? tflag[tpos[e]] : 0;
 }
 
+}  // namespace
+
+CcParams &cc_params() {
+    static CcParams p;
+    return p;
+}
+
+namespace {
+
 int grid_for(int64_t work, int threads) {
     int64_t blocks = ceil_div(work, threads);
     const int64_t cap = int64_t(num_sms()) * (2048 / threads) * 4;
@@ -433,7 +442,8 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     {
         // hook a first slice of the edges, compress every path to its root, then hook the rest:
         // after the compression most finds take one step and most edges meet equal roots at once
-        const int64_t m1 = m < int64_t(n) ? m : int64_t(n);
+        const int64_t slice = int64_t(cc_params().first_slice_quarters) * n / 4;
+        const int64_t m1 = m < slice ? m : (slice > 0 ? slice : 1);
         PhaseTimer pt("br.hook", s);
         k_hook<<<grid_for(m1, 256), 256, 0, s>>>(edges, 0, m1, n, par, is_tree, nullptr, st);
         note_launch();

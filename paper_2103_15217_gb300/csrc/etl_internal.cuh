@@ -146,6 +146,11 @@ struct RankParams {
 };
 RankParams &rank_params();
 
+struct CcParams {
+    int first_slice_quarters = 4;  // edges hooked before the first compression, in units of n/4
+};
+CcParams &cc_params();
+
 struct RmqParams {
     int levels_per_pass = 3;  // 1..3 levels built by one streaming pass
     int block = 256;          // threads per block of the level kernel

@@ -34,6 +34,7 @@ SPACE = [
     ("rank_blocks_per_sm", [4, 8, 16]),
     ("rmq_levels_per_pass", [1, 2, 3]),
     ("rmq_block", [256, 512]),
+    ("cc_first_slice", [2, 8, 16]),
 ]
 
 
