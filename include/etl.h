@@ -103,7 +103,7 @@ typedef struct etl_lca_s *etl_lca_t;
 /*
  * lca_preprocess: parent[0..n) with parent[root] = -1 and every other entry in
  * [0, n) describes one rooted tree (the input format of Sec. 3.2). n in
- * [1, 2^30]. On success *out receives a new handle (host memory, owned by the
+ * [1, 2^30 - 1]. On success *out receives a new handle (host memory, owned by the
  * caller until lca_free). The handle's tables are being built asynchronously
  * on `stream`; queries enqueued on the same stream see them, queries on
  * another stream must wait for it (event or synchronisation). Data errors go
@@ -146,7 +146,7 @@ etl_status lca_query(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q,
  * then occupies preorder positions node_off[i] .. node_off[i+1]-1, so
  * lca_arrays / lca_export return GLOBAL preorder numbers (pre - node_off[i]
  * is the preorder inside tree i; depth and size are per tree). k >= 1,
- * total_n in [k, 2^30].
+ * total_n in [k, 2^30 - 1].
  */
 etl_status lca_preprocess_batch(const int32_t *parent, const int32_t *node_off, int32_t k, int32_t total_n,
                                 int32_t max_n, void *stream, etl_lca_t *out);

@@ -128,6 +128,19 @@ __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restri
     }
 }
 
+// A leaf v's brackets are adjacent in the tour: 2v jumps straight to the successor of 2v+1 with
+// weight 2 (top bit set), and 2v+1 leaves the list. Roots are never contracted.
+__global__ void k_contract_leaves(const int32_t *__restrict__ coff, const int32_t *__restrict__ par, int32_t n,
+                                  int32_t *__restrict__ succ) {
+    for (int64_t t = gtid(); t < n; t += gstride()) {
+        if (coff[t] != coff[t + 1] || par[t] < 0) continue;  // has children, or is a root
+        const int32_t nx = succ[2 * t + 1];
+        if (nx < 0) continue;                               // malformed: leave it to the validity checks
+        succ[2 * t] = int32_t(uint32_t(nx) | 0x80000000u);
+        succ[2 * t + 1] = ETL_END;
+    }
+}
+
 // leave root i -> enter root i+1 (or end of the list after the last tree)
 __global__ void k_link_roots(const int32_t *__restrict__ root_of, int32_t k, int32_t n, int32_t *__restrict__ succ) {
     for (int64_t i = gtid(); i < k; i += gstride()) {
@@ -138,18 +151,26 @@ __global__ void k_link_roots(const int32_t *__restrict__ root_of, int32_t k, int
     }
 }
 
-__global__ void k_node_stats(RankResult rr, int32_t n, int32_t *__restrict__ pre, int32_t *__restrict__ depth,
-                             int32_t *__restrict__ size, int32_t *__restrict__ order, int32_t *__restrict__ status) {
+__global__ void k_node_stats(RankResult rr, const int32_t *__restrict__ succ, int32_t n, int32_t *__restrict__ pre,
+                             int32_t *__restrict__ depth, int32_t *__restrict__ size, int32_t *__restrict__ order,
+                             int32_t *__restrict__ status) {
     const uint4 *pk = reinterpret_cast<const uint4 *>(rr.packed);  // brackets 2v and 2v+1 side by side
     for (int64_t t = gtid(); t < n; t += gstride()) {
-        const uint4 q = pk[t];
+        const bool leaf = succ[2 * t] < ETL_END;  // contracted: the closing bracket is ranked right after
+        uint4 q;
+        if (leaf) {
+            const uint2 a = rr.packed[2 * t];
+            q = make_uint4(a.x, a.y, a.x, 0u);
+        } else {
+            q = pk[t];
+        }
         if (q.x >= rr.rcap || q.z >= rr.rcap) {  // not on the list from the root: malformed input
             set_status(status, ETL_EBADTREE);
             pre[t] = depth[t] = size[t] = -1;
             continue;
         }
         const uint2 in = make_uint2(q.x, q.y), out = make_uint2(q.z, q.w);
-        const int32_t r0 = rank_of(rr, in), r1 = rank_of(rr, out);
+        const int32_t r0 = rank_of(rr, in), r1 = leaf ? r0 + 1 : rank_of(rr, out);
         const int32_t p = evens_before(rr, in);
         pre[t] = p;
         depth[t] = 2 * p - r0;
@@ -337,13 +358,16 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
             note_launch();
             k_link_roots<<<grid_for(k, 256), 256, 0, s>>>(root_of, k, n, succ);
             note_launch();
+            k_contract_leaves<<<grid_for(n, 256), 256, 0, s>>>(coff, par, n, succ);
+            note_launch();
             st = last_launch();
         }
         RankResult rr{};
         if (!st) st = list_rank(succ, 2 * int64_t(n), nullptr, misc, true, 2 * int64_t(n), h->status, ws, &rr);
         if (!st) {
             PhaseTimer pt("lca.node_stats", s);
-            k_node_stats<<<grid_for(n, 256), 256, 0, s>>>(rr, n, h->pre, h->depth, h->size, h->order, h->status);
+            k_node_stats<<<grid_for(n, 256), 256, 0, s>>>(rr, succ, n, h->pre, h->depth, h->size, h->order,
+                                                          h->status);
             note_launch();
             k_check_instances<<<grid_for(k, 256), 256, 0, s>>>(root_of, batch ? h->node_off : nullptr, k, n, h->pre,
                                                                 h->size, h->status);
@@ -387,7 +411,7 @@ using namespace etl;
 extern "C" etl_status lca_preprocess(const int32_t *parent, int32_t n, void *stream, etl_lca_t *out) {
     if (!out) return ETL_EINVAL;
     *out = nullptr;
-    if (!parent || n < 1 || n > (1 << 30)) return ETL_EINVAL;
+    if (!parent || n < 1 || n > (1 << 30) - 1) return ETL_EINVAL;
     return lca_build(parent, n, nullptr, 1, n, true, static_cast<cudaStream_t>(stream), out);
 }
 
@@ -397,7 +421,7 @@ extern "C" etl_status lca_preprocess_ex(const int32_t *parent, int32_t n, int32_
                                         etl_lca_t *out) {
     if (!out) return ETL_EINVAL;
     *out = nullptr;
-    if (!parent || n < 1 || n > (1 << 30) || !(flags & (ETL_LCA_RMQ | ETL_LCA_INLABEL)) ||
+    if (!parent || n < 1 || n > (1 << 30) - 1 || !(flags & (ETL_LCA_RMQ | ETL_LCA_INLABEL)) ||
         (flags & ~(ETL_LCA_RMQ | ETL_LCA_INLABEL)))
         return ETL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -416,7 +440,7 @@ extern "C" etl_status lca_preprocess_batch(const int32_t *parent, const int32_t 
                                            int32_t total_n, int32_t max_n, void *stream, etl_lca_t *out) {
     if (!out) return ETL_EINVAL;
     *out = nullptr;
-    if (!parent || !node_off || k < 1 || total_n < k || total_n > (1 << 30) || max_n < 1 || max_n > total_n)
+    if (!parent || !node_off || k < 1 || total_n < k || total_n > (1 << 30) - 1 || max_n < 1 || max_n > total_n)
         return ETL_EINVAL;
     return lca_build(parent, total_n, node_off, k, max_n, true, static_cast<cudaStream_t>(stream), out);
 }

@@ -24,7 +24,10 @@
 // The "dual" mode also counts even-indexed elements: in the bracket layout
 // of a rooted tree (2v = entering v, 2v+1 = leaving v) that count is the
 // preorder number, so preorder comes straight out of the ranking without a
-// scatter + scan over the tour.
+// scatter + scan over the tour. In dual mode a successor with the top bit
+// set (and not -1) marks a contracted leaf: element 2v of a leaf v stands for
+// both of its brackets (weight 2), the low 31 bits are the successor of 2v+1,
+// and 2v+1 itself is off the list.
 #include <cstdio>
 #include <mutex>
 
@@ -33,7 +36,7 @@
 namespace etl {
 namespace {
 
-constexpr int32_t kLcap = 4096;    // longest walk before a dynamic splitter is opened (< 2^16)
+constexpr int32_t kLcap = 4096;    // longest walk before a dynamic splitter is opened (< 2^16 - 2)
 constexpr int kPjCap = 8192;       // top level solved by one CTA in shared memory
 constexpr int kPjThreads = 1024;
 constexpr int kPjItems = kPjCap / kPjThreads;
@@ -121,9 +124,15 @@ __global__ void k_walk0(const int32_t *__restrict__ succ, int64_t len, const int
         }
         if (active) {
             packed[cur] = make_uint2(uint32_t(sid), lr | (lo << 16));
+            int32_t nxt = __ldg(succ + cur);
             lr += 1;
-            if (DUAL) lo += (cur & 1) == 0 ? 1u : 0u;
-            const int32_t nxt = __ldg(succ + cur);
+            if (DUAL) {
+                lo += (cur & 1) == 0 ? 1u : 0u;
+                if (nxt < ETL_END) {  // contracted leaf: its closing bracket follows at once
+                    nxt &= 0x7fffffff;
+                    lr += 1;
+                }
+            }
             ++steps;
             const bool bad = nxt >= len || nxt < ETL_END || steps > len;
             if (nxt == ETL_END || bad || H.split(uint32_t(nxt))) {
