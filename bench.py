@@ -469,30 +469,67 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
     h2d = sum(t["parent"].numel() * 4 + t["u"].numel() * 8 for t in h_trees) + sum(g["edges"].numel() * 4 for g in h_graphs)
     d2h = sum(t["out"].numel() * 4 for t in h_trees) + sum(g["out"].numel() for g in h_graphs)
 
-    def one():
-        for t in h_trees:
-            p = t["parent"].to(dev, non_blocking=True)
-            u = t["u"].to(dev, non_blocking=True)
-            v = t["v"].to(dev, non_blocking=True)
-            h = etl.lca_preprocess(p)
-            t["out"].copy_(h.query(u, v), non_blocking=True)
-            h.free()
-        for g in h_graphs:
-            e = g["edges"].to(dev, non_blocking=True)
-            g["out"].copy_(etl.find_bridges(e, g["n"]), non_blocking=True)
+    def tree_job(t):
+        p = t["parent"].to(dev, non_blocking=True)
+        u = t["u"].to(dev, non_blocking=True)
+        v = t["v"].to(dev, non_blocking=True)
+        h = etl.lca_preprocess(p)
+        t["out"].copy_(h.query(u, v), non_blocking=True)
+        h.free()
 
-    for _ in range(max(1, args.warmup)):
-        one()
-    torch.cuda.synchronize()
+    def graph_job(g):
+        e = g["edges"].to(dev, non_blocking=True)
+        g["out"].copy_(etl.find_bridges(e, g["n"]), non_blocking=True)
+
+    jobs = [(tree_job, t) for t in h_trees] + [(graph_job, g) for g in h_graphs]
+    side = [torch.cuda.Stream() for _ in jobs]
+
+    def one_sequential():
+        for fn, x in jobs:
+            fn(x)
+
+    def one_pipelined():
+        """Each instance on its own stream (copy in, compute, copy out): the copy engines move one
+        instance's inputs while the SMs work on another's."""
+        for s_, (fn, x) in zip(side, jobs):
+            s_.wait_stream(stream)
+            with torch.cuda.stream(s_):
+                fn(x)
+        for s_ in side:
+            stream.wait_stream(s_)
+
+    def timed(one):
+        for _ in range(max(1, args.warmup)):
+            one()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            one()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / args.steps
+
+    t_seq = max_over_ranks(timed(one_sequential), world, dev)
+    t = max_over_ranks(timed(one_pipelined), world, dev)
+    # copy bandwidth alone, for context: every input of a step in, every result out, nothing else
+    dsts = [torch.empty_like(x[k], device=dev) for _, x in jobs for k in ("parent", "u", "v", "edges") if k in x]
+    srcs = [x[k] for _, x in jobs for k in ("parent", "u", "v", "edges") if k in x]
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(args.steps):
-        one()
+    for i in range(4):
+        if i == 1:
+            a.record(stream)
+        for d_, s_ in zip(dsts, srcs):
+            d_.copy_(s_, non_blocking=True)
     b.record(stream)
     torch.cuda.synchronize()
-    t = a.elapsed_time(b) / 1e3 / args.steps
+    h2d_s = a.elapsed_time(b) / 1e3 / 3
+    del dsts
     return {"value": units * world / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": t * 1e3}
+            "ms_per_step": t * 1e3, "sequential_ms_per_step": t_seq * 1e3,
+            "h2d_only_ms_per_step": h2d_s * 1e3, "h2d_gb_per_s": h2d / h2d_s / 1e9,
+            "timing": "public API calls, eager; each instance on its own stream (copy in, compute, copy out); "
+                      "host inputs pinned"}
 
 
 # ------------------------------------------------------------------ batched instances
@@ -662,11 +699,24 @@ def compare_methods(parent_np, u_np, v_np, dev, naive_step_budget=2e9):
     t_nv_pre = _median_ms(lambda: etl.NaiveLca(P))
     out_n = torch.empty(qn, dtype=torch.int32, device=dev)
     t_nv_q = _median_ms(lambda: nv.query(U[:qn], V[:qn], out=out_n), reps=2)
-    agree = bool(torch.equal(out_r, out_i) and torch.equal(out_r[:qn], out_n))
+    # the same RMQ method on a full sparse table (n log n entries) instead of the blocked one
+    blocked0 = etl.tune_get()["rmq_blocked"]
+    etl.tune_set(rmq_blocked=0)
+    try:
+        hf = etl.lca_preprocess(P)
+        out_f = torch.empty_like(U)
+        t_full_pre = _median_ms(pre_rmq)
+        t_full_q = _median_ms(lambda: hf.query(U, V, out=out_f))
+        hf.free()
+    finally:
+        etl.tune_set(rmq_blocked=blocked0)
+    agree = bool(torch.equal(out_r, out_i) and torch.equal(out_r[:qn], out_n) and torch.equal(out_r, out_f))
     h.free()
     res.update({
         "avg_depth": depth_mean,
-        "rmq": {"preprocess_ms": t_rmq_pre, "query_ms": t_rmq_q, "queries_per_s": q / t_rmq_q * 1e3},
+        "rmq": {"preprocess_ms": t_rmq_pre, "query_ms": t_rmq_q, "queries_per_s": q / t_rmq_q * 1e3,
+                "table": "blocked" if blocked0 else "full"},
+        "rmq_full_table": {"preprocess_ms": t_full_pre, "query_ms": t_full_q, "queries_per_s": q / t_full_q * 1e3},
         "inlabel": {"preprocess_ms": t_inl_pre, "query_ms": t_inl_q, "queries_per_s": q / t_inl_q * 1e3},
         "naive": {"preprocess_ms": t_nv_pre, "queries_timed": qn, "query_ms_for_timed": t_nv_q,
                   "queries_per_s": qn / t_nv_q * 1e3, "query_ms_for_all_q_est": t_nv_q * q / qn},
@@ -686,9 +736,17 @@ def compare_bridge_methods(edges_np, n, dev):
     torch.cuda.synchronize()
     t_tv = _median_ms(lambda: etl.find_bridges(E, n))
     t_hy = _median_ms(lambda: etl.find_bridges(E, n, method="hybrid"))
+    blocked0 = etl.tune_get()["rmq_blocked"]
+    etl.tune_set(rmq_blocked=0)
+    try:
+        c = etl.find_bridges(E, n)
+        t_full = _median_ms(lambda: etl.find_bridges(E, n))
+    finally:
+        etl.tune_set(rmq_blocked=blocked0)
     m = edges_np.shape[0]
-    return {"n": n, "m": m, "tv_ms": t_tv, "hybrid_ms": t_hy, "tv_edges_per_s": m / t_tv * 1e3,
-            "hybrid_edges_per_s": m / t_hy * 1e3, "masks_identical": bool(torch.equal(a, b))}
+    return {"n": n, "m": m, "tv_ms": t_tv, "hybrid_ms": t_hy, "tv_full_tables_ms": t_full,
+            "tv_edges_per_s": m / t_tv * 1e3, "hybrid_edges_per_s": m / t_hy * 1e3,
+            "masks_identical": bool(torch.equal(a, b) and torch.equal(a, c))}
 
 
 def run_methods(args, dev, trees=None):

@@ -92,9 +92,10 @@ etl_status etl_list_rank_static(const int32_t *succ, int64_t len, int32_t head, 
 /* ------------------------------------------------------------------ LCA
  * Lowest common ancestors (Sec. 3): preprocessing builds the Euler tour of the
  * tree (Sec. 2.1, successor = next(twin)), ranks it once (Sec. 2.2), derives
- * preorder, depth and subtree size from the ranks, and builds a sparse table
- * for range-minimum queries over the preorder sequence (the RMQ reduction of
- * Sec. 3.1). A query is then answered in O(1) with two table reads.
+ * preorder, depth and subtree size from the ranks, and builds a range-minimum
+ * table over the preorder sequence (the RMQ reduction of Sec. 3.1): a blocked
+ * two-level table by default, else a full sparse table (ETL_TUNE_RMQ_BLOCKED).
+ * A query is then answered in O(1) with a few table reads.
  *
  * Opaque handle; it owns the device arrays of one preprocessed tree.
  */
@@ -114,7 +115,7 @@ etl_status lca_preprocess(const int32_t *parent, int32_t n, void *stream, etl_lc
 
 /*
  * lca_preprocess_ex: as lca_preprocess, choosing which query structures to
- * build: ETL_LCA_RMQ (the sparse table, for lca_query) and/or
+ * build: ETL_LCA_RMQ (the range-minimum table, for lca_query) and/or
  * ETL_LCA_INLABEL (the Inlabel records, for lca_query_inlabel; the paper's
  * GPU method, O(n) memory). Unknown bits or neither bit: ETL_EINVAL.
  */
@@ -141,7 +142,7 @@ etl_status lca_query(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q,
  * node_off[i+1]-1, its nodes are numbered 0 .. size-1 and its root has -1.
  * node_off is a DEVICE int32[k+1] array with node_off[0] = 0, node_off[k] =
  * total_n and every tree non-empty (else ETL_EINVAL in the status word).
- * max_n (host) must be >= the largest tree's size; it sizes the sparse table.
+ * max_n (host) must be >= the largest tree's size; it sizes the range-minimum table.
  * The trees' Euler tours are chained into one list and ranked once; tree i
  * then occupies preorder positions node_off[i] .. node_off[i+1]-1, so
  * lca_arrays / lca_export return GLOBAL preorder numbers (pre - node_off[i]
@@ -256,6 +257,12 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  *   ETL_TUNE_CC_FIRST_SLICE edges hooked before the first compression of the
  *                           connected-components pass, in units of n/4,
  *                           1..64 (4, i.e. n edges)
+ *   ETL_TUNE_RMQ_BLOCKED    1: range-min / max tables are blocked two-level
+ *                           tables (prefix / suffix results inside blocks of
+ *                           32 entries plus a sparse table over the blocks,
+ *                           O(n) memory); 0: full sparse tables (n log n
+ *                           entries). Both answer every query exactly. (1)
+ *                           Read when a handle or a bridge call is built.
  * Unknown keys or out-of-range values return ETL_EINVAL.
  */
 enum {
@@ -265,7 +272,8 @@ enum {
     ETL_TUNE_RANK_BLOCKS_PER_SM = 4,
     ETL_TUNE_RMQ_LEVELS_PER_PASS = 5,
     ETL_TUNE_RMQ_BLOCK = 6,
-    ETL_TUNE_CC_FIRST_SLICE = 7
+    ETL_TUNE_CC_FIRST_SLICE = 7,
+    ETL_TUNE_RMQ_BLOCKED = 8
 };
 etl_status etl_tune_set(int32_t key, int32_t value);
 etl_status etl_tune_get(int32_t key, int32_t *value);

@@ -31,7 +31,8 @@ EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_pr
            "lca_preprocess_ex", "etl_trim", "two_edge_cc", "find_bridges_hybrid", "etl_profile_enable", "etl_profile_reset",
            "etl_profile_count", "etl_profile_get", "etl_launch_count", "etl_tune_set", "etl_tune_get")
 TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
-             "rmq_levels_per_pass": 5, "rmq_block": 6, "cc_first_slice": 7}
+             "rmq_levels_per_pass": 5, "rmq_block": 6, "cc_first_slice": 7,
+             "rmq_blocked": 8}
 
 _lock = threading.Lock()
 _lib = None
@@ -229,7 +230,7 @@ def profile_enable(on: bool = True):
 
 
 def tune_set(**params):
-    """Set launch parameters (no effect on results): rank_k0_log2, rank_k_log2, rank_block, rank_blocks_per_sm."""
+    """Set launch parameters and table forms (no effect on results); names as in TUNE_KEYS."""
     lib = load_library()
     for k, v in params.items():
         _check(f"etl_tune_set({k})", lib.etl_tune_set(TUNE_KEYS[k], int(v)))

@@ -122,6 +122,10 @@ extern "C" etl_status etl_tune_set(int32_t key, int32_t value) {
             if (value < 1 || value > 64) return ETL_EINVAL;
             cc_params().first_slice_quarters = value;
             return ETL_OK;
+        case ETL_TUNE_RMQ_BLOCKED:
+            if (value != 0 && value != 1) return ETL_EINVAL;
+            rmq_params().blocked = value != 0;
+            return ETL_OK;
         default:
             return ETL_EINVAL;
     }
@@ -138,6 +142,7 @@ extern "C" etl_status etl_tune_get(int32_t key, int32_t *value) {
         case ETL_TUNE_RMQ_LEVELS_PER_PASS: *value = rmq_params().levels_per_pass; return ETL_OK;
         case ETL_TUNE_RMQ_BLOCK: *value = rmq_params().block; return ETL_OK;
         case ETL_TUNE_CC_FIRST_SLICE: *value = cc_params().first_slice_quarters; return ETL_OK;
+        case ETL_TUNE_RMQ_BLOCKED: *value = rmq_params().blocked ? 1 : 0; return ETL_OK;
         default: return ETL_EINVAL;
     }
 }

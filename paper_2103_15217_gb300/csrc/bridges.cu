@@ -263,6 +263,37 @@ __global__ void k_place(const int32_t *__restrict__ d_arcs, const int32_t *__res
     }
 }
 
+// blocked form: L and H interleaved (x = L, y = H) in one table of int2
+__global__ void k_place2(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ child,
+                         const int32_t *__restrict__ etin, const int32_t *__restrict__ etout,
+                         const int32_t *__restrict__ nlo, const int32_t *__restrict__ nhi, int64_t P,
+                         int2 *__restrict__ LH) {
+    const int64_t T = *d_arcs / 2;
+    const int2 id = make_int2(INT_MAX, INT_MIN);
+    if (blockIdx.x == 0 && threadIdx.x == 0) LH[0] = id;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t c = child[t], a = etin[t], b = etout[t];
+        if (a < 0 || b >= P || a >= b) continue;
+        LH[a] = make_int2(nlo[c], nhi[c]);
+        LH[b] = id;
+    }
+}
+
+__global__ void k_bridge_test2(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ etin,
+                               const int32_t *__restrict__ etout, BlockedView<OpMinMax> lh, int64_t P,
+                               uint8_t *__restrict__ tflag) {
+    const int64_t T = *d_arcs / 2;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t a = etin[t], b = etout[t];
+        if (a < 0 || b >= P || a >= b) {
+            tflag[t] = 0;
+            continue;
+        }
+        const int2 r = blocked_query<OpMinMax>(lh, a, b);  // (low, high) of the subtree
+        tflag[t] = (r.x >= a && r.y <= b) ? 1 : 0;
+    }
+}
+
 __global__ void k_bridge_test(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ etin,
                               const int32_t *__restrict__ etout, const int32_t *__restrict__ Lt,
                               const int32_t *__restrict__ Ht, int64_t P, int64_t ld, uint8_t *__restrict__ tflag) {
@@ -309,7 +340,6 @@ int grid_for(int64_t work, int threads) {
 namespace etl {
 namespace {
 
-// the whole Tarjan-Vishkin pipeline on a graph with global ids; st is a zeroed device status word
 // ---- the hybrid of Sec. 4.3: parents and levels of the rooted forest from its Euler tour, then
 // Chaitanya-Kothapalli marking: every non-tree edge walks both ends up to their LCA and marks the
 // tree edges on the way (a tree edge is named by its child); unmarked tree edges are bridges
@@ -410,6 +440,7 @@ etl_status hybrid_marking(const int32_t *edges, int64_t m, int32_t n, const uint
     return last_launch();
 }
 
+// the whole Tarjan-Vishkin pipeline on a graph with global ids; st is a zeroed device status word.
 // hybrid: instead of low / high, the Chaitanya-Kothapalli marking on the same rooted forest
 etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *st,
                         Workspace &ws, bool hybrid = false) {
@@ -419,6 +450,8 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     const int64_t P = N;                    // tour positions 0 .. A
     const int levels = sparse_levels(P);
     const int64_t ld = sparse_ld(P);
+    const bool blocked = rmq_params().blocked;
+    const BlockedLayout bl = blocked_layout(P, P);
     int32_t *par = ws.get<int32_t>(n), *deg = ws.get<int32_t>(n), *off = ws.get<int32_t>(int64_t(n) + 1);
     int2 *B = ws.get<int2>(A > 0 ? A : 1);
     int32_t *tin = ws.get<int32_t>(n), *nlo = ws.get<int32_t>(n), *nhi = ws.get<int32_t>(n);
@@ -429,8 +462,9 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     int32_t *succ = ws.get<int32_t>(N);
     int32_t *child = ws.get<int32_t>(n), *etin = ws.get<int32_t>(n), *etout = ws.get<int32_t>(n);
     uint8_t *tflag = ws.get<uint8_t>(n);
-    int32_t *Lt = hybrid ? nullptr : ws.get<int32_t>(ld * levels);
-    int32_t *Ht = hybrid ? nullptr : ws.get<int32_t>(ld * levels);
+    int32_t *Lt = (hybrid || blocked) ? nullptr : ws.get<int32_t>(ld * levels);
+    int32_t *Ht = (hybrid || blocked) ? nullptr : ws.get<int32_t>(ld * levels);
+    int2 *LH = (!hybrid && blocked) ? ws.get<int2>(bl.elems()) : nullptr;
     if (!ws.ok()) return ETL_ENOMEM;
     etl_status rc = ETL_OK;
     const int gn = grid_for(n, 256), gm = grid_for(m, 256), gA = grid_for(N, 256);
@@ -521,15 +555,26 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
         note_launch();
         k_nontree_minmax<<<gm, 256, 0, s>>>(edges, m, n, is_tree, tin, nlo, nhi);
         note_launch();
-        k_place<<<gt, 256, 0, s>>>(n_arcs, child, etin, etout, nlo, nhi, P, Lt, Ht);
+        if (blocked)
+            k_place2<<<gt, 256, 0, s>>>(n_arcs, child, etin, etout, nlo, nhi, P, LH);
+        else
+            k_place<<<gt, 256, 0, s>>>(n_arcs, child, etin, etout, nlo, nhi, P, Lt, Ht);
         note_launch();
         rc = last_launch();
     }
-    if (!rc) rc = sparse_table_build<false>(Lt, P, levels, s);
-    if (!rc) rc = sparse_table_build<true>(Ht, P, levels, s);
+    if (blocked) {
+        if (!rc) rc = blocked_build<OpMinMax>(LH, P, bl, s);
+    } else {
+        if (!rc) rc = sparse_table_build<false>(Lt, P, levels, s);
+        if (!rc) rc = sparse_table_build<true>(Ht, P, levels, s);
+    }
     if (!rc) {
         PhaseTimer pt("br.test", s);
-        k_bridge_test<<<grid_for(n, 256), 256, 0, s>>>(n_arcs, etin, etout, Lt, Ht, P, ld, tflag);
+        if (blocked)
+            k_bridge_test2<<<grid_for(n, 256), 256, 0, s>>>(n_arcs, etin, etout, blocked_view<OpMinMax>(LH, bl), P,
+                                                           tflag);
+        else
+            k_bridge_test<<<grid_for(n, 256), 256, 0, s>>>(n_arcs, etin, etout, Lt, Ht, P, ld, tflag);
         note_launch();
         k_finalize<<<gm, 256, 0, s>>>(m, is_tree, tpos, tflag, st, is_bridge);
         note_launch();

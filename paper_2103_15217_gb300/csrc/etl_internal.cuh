@@ -154,6 +154,7 @@ CcParams &cc_params();
 struct RmqParams {
     int levels_per_pass = 3;  // 1..3 levels built by one streaming pass
     int block = 256;          // threads per block of the level kernel
+    bool blocked = true;      // two-level (blocked) tables instead of full sparse tables
 };
 RmqParams &rmq_params();
 
@@ -195,6 +196,83 @@ __device__ __forceinline__ int32_t sparse_query(const int32_t *__restrict__ tabl
     return IS_MAX ? max(a, b) : min(a, b);
 }
 
+// ----------------------------------------------------------------- blocked range-min / max tables
+//
+// Two levels over x[0..n): x is cut into blocks of 32 entries; pm[i] / sm[i]
+// hold op over x from the start of i's block to i / from i to the end of its
+// block, and `top` is a full sparse table over the nblk block results. A range
+// [lo, hi] inside one block is answered from x directly (at most 32 entries of
+// one 128-byte line); otherwise it is op(sm[lo], pm[hi]) plus, when whole
+// blocks lie between, one query of `top`. The build reads x once and writes
+// 2n + O(n / 32 * log n) entries; `top` (n / 32 entries per level) stays in L2.
+// Layout of one allocation of element type T: x, pm, sm (nblk * 32 entries
+// each, x padded with the identity by the build) then tlevels rows of `top`,
+// nblk entries apart.
+
+struct OpMin {
+    using T = int32_t;
+    __device__ static __forceinline__ T id() { return INT32_MAX; }
+    __device__ static __forceinline__ T f(T a, T b) { return min(a, b); }
+};
+struct OpMax {
+    using T = int32_t;
+    __device__ static __forceinline__ T id() { return INT32_MIN; }
+    __device__ static __forceinline__ T f(T a, T b) { return max(a, b); }
+};
+struct OpMinMax {  // x = min of the first component, y = max of the second
+    using T = int2;
+    __device__ static __forceinline__ T id() { return make_int2(INT32_MAX, INT32_MIN); }
+    __device__ static __forceinline__ T f(T a, T b) { return make_int2(min(a.x, b.x), max(a.y, b.y)); }
+};
+
+constexpr int kRmqBlockLog2 = 5;
+constexpr int kRmqBlock = 1 << kRmqBlockLog2;
+
+struct BlockedLayout {
+    int64_t nblk;  // blocks of 32 entries
+    int tlevels;   // levels of the top table
+    int64_t elems() const { return 3 * nblk * kRmqBlock + nblk * tlevels; }
+};
+// a table over n entries answering ranges of up to max_len entries
+BlockedLayout blocked_layout(int64_t n, int64_t max_len);
+// x (first n entries of base) must be filled; builds pad, pm, sm and top
+template <class Op>
+etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L, cudaStream_t s);
+
+template <class Op>
+struct BlockedView {
+    const typename Op::T *x, *pm, *sm, *top;
+    int64_t nblk;
+    int tlevels;
+};
+template <class Op>
+inline BlockedView<Op> blocked_view(const typename Op::T *base, const BlockedLayout &L) {
+    const int64_t N = L.nblk * kRmqBlock;
+    return BlockedView<Op>{base, base + N, base + 2 * N, base + 3 * N, L.nblk, L.tlevels};
+}
+// longest range a layout answers (a range of len entries spans at most (len - 1) / 32 whole blocks)
+inline int64_t blocked_max_len(const BlockedLayout &L) { return (int64_t(kRmqBlock) << L.tlevels) - 1; }
+
+template <class Op>
+__device__ __forceinline__ typename Op::T blocked_query(const BlockedView<Op> &t, int32_t lo,
+                                                        int32_t hi) {  // inclusive, lo <= hi
+    using T = typename Op::T;
+    const int32_t bl = lo >> kRmqBlockLog2, bh = hi >> kRmqBlockLog2;
+    if (bl == bh) {
+        T m = __ldg(t.x + lo);
+        for (int32_t j = lo + 1; j <= hi; ++j) m = Op::f(m, __ldg(t.x + j));
+        return m;
+    }
+    T m = Op::f(__ldg(t.sm + lo), __ldg(t.pm + hi));
+    if (bh - bl > 1) {
+        const int32_t a = bl + 1, b = bh - 1;
+        const int l = 31 - __clz(b - a + 1);
+        const T *row = t.top + int64_t(l) * t.nblk;
+        m = Op::f(m, Op::f(__ldg(row + a), __ldg(row + b - (1 << l) + 1)));
+    }
+    return m;
+}
+
 }  // namespace etl
 
 // ----------------------------------------------------------------- the LCA handle
@@ -206,7 +284,9 @@ struct etl_lca_s {
     cudaStream_t stream = nullptr;
     int32_t *pre = nullptr, *depth = nullptr, *size = nullptr, *order = nullptr;
     int64_t ld = 0;             // row length of the sparse table
-    int32_t *table = nullptr;   // levels * ld
+    int32_t *table = nullptr;   // levels * ld (full sparse table) or the blocked table's allocation
+    bool blocked = false;       // table is a blocked two-level table (layout `bl`)
+    etl::BlockedLayout bl{};
     int32_t *status = nullptr;  // device status word
     bool has_table = false;     // RMQ sparse table built (lca_query available)
     void *inrec = nullptr;      // Inlabel: per node (inlabel, ascendant, depth, parent), int4[n]

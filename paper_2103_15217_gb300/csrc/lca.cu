@@ -22,10 +22,12 @@
 //      prefix sum of Sec. 2); size = (rank(2v+1) - rank(2v) + 1) / 2. In a
 //      chained batch, tree i occupies preorder positions node_off[i] ..
 //      node_off[i+1]-1 and depth / size come out per tree.
-//   6. k_parent_pre: Q[pre(v)] = pre(parent(v)), level 0 of the sparse table
-//      (a separate pass: gathering pre[] is cheaper than re-deriving the
+//   6. k_parent_pre: Q[pre(v)] = pre(parent(v)), level 0 of the range-minimum
+//      table (a separate pass: gathering pre[] is cheaper than re-deriving the
 //      parent's preorder from its bracket record).
-//   7. sparse table over Q (rmq.cu), as many levels as the largest tree needs.
+//   7. range-minimum table over Q (rmq.cu): by default the blocked two-level
+//      table (in-block prefix / suffix minima plus a sparse table over blocks
+//      of 32), else a full sparse table; sized for the largest tree.
 //
 // Query: for u != v with i = min(pre u, pre v), j = max(...), every node with
 // preorder in (i, j] is a proper descendant of LCA(u, v), and the child of the
@@ -202,6 +204,8 @@ struct LcaView {
     int32_t n, k, levels;
     int64_t ld;
     const int32_t *pre, *order, *table, *hstatus, *off;
+    BlockedView<OpMin> bv;  // the blocked table (when built instead of the full one)
+    int64_t max_len;        // longest range the table answers
 };
 
 constexpr int kQueryIlp = 4;
@@ -209,7 +213,7 @@ constexpr int kQueryIlp = 4;
 // Each thread answers kQueryIlp queries at once so that their dependent
 // gathers (pre, table, order) overlap in flight. BATCH: ids are local to the
 // instance inst[i] and so is the answer.
-template <bool BATCH>
+template <bool BATCH, bool BLOCKED>
 __global__ void __launch_bounds__(256)
     k_lca_query(LcaView h, const int32_t *__restrict__ inst, const int32_t *__restrict__ u,
                 const int32_t *__restrict__ v, int64_t q, int32_t *__restrict__ out, int32_t *__restrict__ status) {
@@ -252,13 +256,15 @@ __global__ void __launch_bounds__(256)
                 const int32_t pa = __ldg(h.pre + ofs[k] + a[k]), pb = __ldg(h.pre + ofs[k] + b[k]);
                 lo[k] = min(pa, pb) + 1;
                 hi[k] = max(pa, pb);
-                need[k] = (31 - __clz(hi[k] - lo[k] + 1)) < h.levels;  // cannot fail unless max_n was understated
+                need[k] = hi[k] - lo[k] + 1 <= h.max_len;  // cannot fail unless max_n was understated
                 if (!need[k]) set_status(status, ETL_EINVAL);
             }
         }
 #pragma unroll
         for (int k = 0; k < kQueryIlp; ++k)
-            if (need[k]) lo[k] = sparse_query<false>(h.table, h.ld, lo[k], hi[k]);
+            if (need[k])
+                lo[k] = BLOCKED ? blocked_query<OpMin>(h.bv, lo[k], hi[k])
+                                : sparse_query<false>(h.table, h.ld, lo[k], hi[k]);
 #pragma unroll
         for (int k = 0; k < kQueryIlp; ++k) {
             const int64_t i = base + k * stride;
@@ -297,14 +303,16 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
     h->levels = max_n > 1 ? sparse_levels(max_n - 1) : 1;
     h->has_table = with_table;
     h->ld = sparse_ld(n);
+    h->blocked = rmq_params().blocked;
+    h->bl = blocked_layout(n, max_n);
+    const size_t table_entries = h->blocked ? size_t(h->bl.elems()) : size_t(h->ld) * size_t(h->levels);
     const size_t nb = size_t(n) * sizeof(int32_t);
     bool ok = dev_alloc((void **)&h->pre, nb, s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->depth, nb, s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->size, nb, s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->order, nb, s) == cudaSuccess;
     if (with_table)
-        ok = ok && dev_alloc((void **)&h->table, size_t(h->ld) * sizeof(int32_t) * size_t(h->levels), s) ==
-                       cudaSuccess;
+        ok = ok && dev_alloc((void **)&h->table, table_entries * sizeof(int32_t), s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->status, sizeof(int32_t), s) == cudaSuccess;
     if (ok && batch)
         ok = dev_alloc((void **)&h->node_off, size_t(k + 1) * sizeof(int32_t), s) == cudaSuccess;
@@ -380,7 +388,9 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
             note_launch();
             st = last_launch();
         }
-        if (!st && with_table) st = sparse_table_build<false>(h->table, n, h->levels, s);
+        if (!st && with_table)
+            st = h->blocked ? blocked_build<OpMin>(h->table, n, h->bl, s)
+                            : sparse_table_build<false>(h->table, n, h->levels, s);
     }
     if (st) {
         free_handle(h);
@@ -392,13 +402,23 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
 
 etl_status query_launch(etl_lca_t h, const int32_t *inst, const int32_t *u, const int32_t *v, int64_t q,
                         int32_t *out, int32_t *status, cudaStream_t s) {
-    LcaView view{h->n, h->k, h->levels, h->ld, h->pre, h->order, h->table, h->status, h->node_off};
+    LcaView view{h->n,     h->k,      h->levels, h->ld,
+                 h->pre,   h->order,  h->table,  h->status,
+                 h->node_off, blocked_view<OpMin>(h->table, h->bl),
+                 h->blocked ? blocked_max_len(h->bl) : (int64_t(1) << h->levels) - 1};
     PhaseTimer pt("lca.query", s);
     const int grid = grid_for(ceil_div(q, kQueryIlp), 256);
-    if (inst)
-        k_lca_query<true><<<grid, 256, 0, s>>>(view, inst, u, v, q, out, status);
-    else
-        k_lca_query<false><<<grid, 256, 0, s>>>(view, nullptr, u, v, q, out, status);
+    if (h->blocked) {
+        if (inst)
+            k_lca_query<true, true><<<grid, 256, 0, s>>>(view, inst, u, v, q, out, status);
+        else
+            k_lca_query<false, true><<<grid, 256, 0, s>>>(view, nullptr, u, v, q, out, status);
+    } else {
+        if (inst)
+            k_lca_query<true, false><<<grid, 256, 0, s>>>(view, inst, u, v, q, out, status);
+        else
+            k_lca_query<false, false><<<grid, 256, 0, s>>>(view, nullptr, u, v, q, out, status);
+    }
     note_launch();
     return last_launch();
 }

@@ -1,6 +1,9 @@
 // Sparse tables for range-minimum / range-maximum queries (Sec. 3.1 reduces
-// LCA to RMQ; Sec. 4.1 aggregates low / high over subtrees by RMQ).
+// LCA to RMQ; Sec. 4.1 aggregates low / high over subtrees by RMQ), full and
+// blocked (two-level: in-block prefix / suffix results plus a full table over
+// the blocks, declared in etl_internal.cuh).
 //
+// Full tables:
 // Level l holds op over x[i .. i + 2^l). One streaming pass builds up to three
 // consecutive levels l, l+1, l+2 from level l-1: with h = 2^(l-1),
 //     T_l[i]   = op(p[i], p[i+h])
@@ -73,7 +76,104 @@ __global__ void k_pad(int32_t *__restrict__ table, int64_t n, int64_t ld) {
     if (i < ld) table[i] = IS_MAX ? INT_MIN : INT_MAX;
 }
 
+// ---- blocked tables
+
+__device__ __forceinline__ int32_t shfl_up(int32_t v, int d) { return __shfl_up_sync(kFull, v, d); }
+__device__ __forceinline__ int2 shfl_up(int2 v, int d) {
+    return make_int2(__shfl_up_sync(kFull, v.x, d), __shfl_up_sync(kFull, v.y, d));
+}
+__device__ __forceinline__ int32_t shfl_down(int32_t v, int d) { return __shfl_down_sync(kFull, v, d); }
+__device__ __forceinline__ int2 shfl_down(int2 v, int d) {
+    return make_int2(__shfl_down_sync(kFull, v.x, d), __shfl_down_sync(kFull, v.y, d));
+}
+
+// one warp per block of 32 entries: prefix and suffix op by shuffles, block result -> top level 0;
+// entries in [n, nblk * 32) are set to the identity first
+template <class Op>
+__global__ void k_block_scan(typename Op::T *__restrict__ x, int64_t n, int64_t nblk, typename Op::T *__restrict__ pm,
+                             typename Op::T *__restrict__ sm, typename Op::T *__restrict__ top0) {
+    using T = typename Op::T;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t b = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; b < nblk; b += warps) {
+        const int64_t i = b * kRmqBlock + lane;
+        T v;
+        if (i < n) {
+            v = x[i];
+        } else {
+            v = Op::id();
+            x[i] = v;
+        }
+        T p = v, q = v;
+#pragma unroll
+        for (int d = 1; d < kRmqBlock; d <<= 1) {
+            const T up = shfl_up(p, d), dn = shfl_down(q, d);
+            if (lane >= d) p = Op::f(p, up);
+            if (lane + d < kRmqBlock) q = Op::f(q, dn);
+        }
+        pm[i] = p;
+        sm[i] = q;
+        if (lane == kRmqBlock - 1) top0[b] = p;
+    }
+}
+
+// levels l .. l + count - 1 of the top table from level l - 1 (rows nblk apart, count <= 3)
+template <class Op>
+__global__ void k_top_levels(typename Op::T *__restrict__ top, int64_t nblk, int l, int count) {
+    using T = typename Op::T;
+    const T *p = top + int64_t(l - 1) * nblk;
+    const int64_t h = int64_t(1) << (l - 1);
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nblk; i += int64_t(gridDim.x) * blockDim.x) {
+        T m = Op::f(p[i], i + h < nblk ? p[i + h] : Op::id());
+        top[int64_t(l) * nblk + i] = m;
+        for (int c = 1; c < count; ++c) {
+            const int64_t w = h << c;  // the next level adds the 2^c shifted entries w .. 2w - 1 (steps of h)
+            for (int64_t j = w; j < 2 * w; j += h) m = Op::f(m, i + j < nblk ? p[i + j] : Op::id());
+            top[int64_t(l + c) * nblk + i] = m;
+        }
+    }
+}
+
 }  // namespace
+
+BlockedLayout blocked_layout(int64_t n, int64_t max_len) {
+    BlockedLayout L;
+    L.nblk = ceil_div(n < 1 ? 1 : n, kRmqBlock);
+    const int64_t span = ceil_div(max_len < 1 ? 1 : max_len, kRmqBlock);  // whole blocks a range may cover, + 1
+    L.tlevels = sparse_levels(span < L.nblk ? span : L.nblk);
+    return L;
+}
+
+template <class Op>
+etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L, cudaStream_t s) {
+    using T = typename Op::T;
+    const int64_t N = L.nblk * kRmqBlock;
+    T *top = base + 3 * N;
+    const int grid_cap = num_sms() * 8;
+    {
+        PhaseTimer pt("rmq.blocks", s);
+        int blocks = int(ceil_div(N, 256));
+        if (blocks > grid_cap) blocks = grid_cap;
+        k_block_scan<Op><<<blocks, 256, 0, s>>>(base, n, L.nblk, base + N, base + 2 * N, top);
+        note_launch();
+    }
+    etl_status st = last_launch();
+    for (int l = 1; !st && l < L.tlevels;) {
+        const int count = L.tlevels - l >= 3 ? 3 : L.tlevels - l;
+        int blocks = int(ceil_div(L.nblk, 256));
+        if (blocks > grid_cap) blocks = grid_cap;
+        PhaseTimer pt("rmq.top", s);
+        k_top_levels<Op><<<blocks, 256, 0, s>>>(top, L.nblk, l, count);
+        note_launch();
+        st = last_launch();
+        l += count;
+    }
+    return st;
+}
+
+template etl_status blocked_build<OpMin>(int32_t *, int64_t, const BlockedLayout &, cudaStream_t);
+template etl_status blocked_build<OpMax>(int32_t *, int64_t, const BlockedLayout &, cudaStream_t);
+template etl_status blocked_build<OpMinMax>(int2 *, int64_t, const BlockedLayout &, cudaStream_t);
 
 RmqParams &rmq_params() {
     static RmqParams p;

@@ -39,7 +39,7 @@ from . import find_bridges_batch, lca_preprocess_batch
 
 LCA_BYTES_PER_QUERY = 16          # inst, u, v, out (int32)
 GRAPH_BYTES_PER_EDGE = 48         # edges, flags, prefix sums, masks, staging
-GRAPH_BYTES_PER_NODE = 520        # union-find, tour, ranking, two sparse tables over 2n positions
+GRAPH_BYTES_PER_NODE = 520        # union-find, tour, ranking, low / high tables over 2n positions (full form)
 
 
 @dataclasses.dataclass
@@ -87,9 +87,15 @@ class _Batch:
         self.t_admit = 0.0
 
 
-def resident_bytes(sizes) -> int:
-    """Device bytes of a resident batch handle over trees of these sizes."""
+def resident_bytes(sizes, blocked: bool = True) -> int:
+    """Device bytes of a resident batch handle over trees of these sizes: pre, depth, size, order and
+    the range-minimum table (blocked: three arrays of n plus a sparse table over blocks of 32;
+    full: one row of n per level)."""
     n = int(sum(sizes))
+    if blocked:
+        nblk = (n + 31) // 32
+        levels = int(np.ceil(np.log2(max(2, (max(sizes) + 31) // 32 + 1)))) + 1
+        return 16 * n + 4 * (3 * nblk * 32 + nblk * levels)
     levels = int(np.ceil(np.log2(max(2, max(sizes))))) + 1
     return 16 * n + 4 * ((n + 3) // 4 * 4) * levels
 
@@ -103,7 +109,8 @@ class Server:
         off = np.zeros(len(sizes) + 1, np.int32)
         off[1:] = np.cumsum(sizes)
         self.budget = int(budget_bytes)
-        self.resident = resident_bytes(sizes)
+        from . import tune_get
+        self.resident = resident_bytes(sizes, blocked=bool(tune_get()["rmq_blocked"]))
         if self.resident > self.budget:
             raise ValueError("resident trees alone exceed the HBM budget")
         parent = torch.from_numpy(np.concatenate(tree_parents).astype(np.int32)).to(self.dev)

@@ -35,6 +35,7 @@ SPACE = [
     ("rmq_levels_per_pass", [1, 2, 3]),
     ("rmq_block", [256, 512]),
     ("cc_first_slice", [2, 8, 16]),
+    ("rmq_blocked", [0, 1]),
 ]
 
 
