@@ -22,9 +22,9 @@
 //      prefix sum of Sec. 2); size = (rank(2v+1) - rank(2v) + 1) / 2. In a
 //      chained batch, tree i occupies preorder positions node_off[i] ..
 //      node_off[i+1]-1 and depth / size come out per tree.
-//   6. k_parent_pre: Q[pre(v)] = pre(parent(v)), level 0 of the range-minimum
-//      table (a separate pass: gathering pre[] is cheaper than re-deriving the
-//      parent's preorder from its bracket record).
+//   6. k_parent_pre: Q[i] = pre(parent(order[i])), level 0 of the range-minimum
+//      table, written in preorder (a separate pass: gathering pre[] is cheaper
+//      than re-deriving the parent's preorder from its bracket record).
 //   7. range-minimum table over Q (rmq.cu): by default the blocked two-level
 //      table (in-block prefix / suffix minima plus a sparse table over blocks
 //      of 32), else a full sparse table; sized for the largest tree.
@@ -181,11 +181,15 @@ __global__ void k_node_stats(RankResult rr, const int32_t *__restrict__ succ, in
     }
 }
 
-__global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *__restrict__ pre, int32_t n,
-                             int32_t *__restrict__ q0) {
-    for (int64_t v = gtid(); v < n; v += gstride()) {
-        const int32_t i = pre[v], p = parent[v];
-        if (i >= 0 && i < n) q0[i] = (p >= 0 && p < n) ? __ldg(pre + p) : -1;  // root: never inside a range
+// Q in preorder: position i holds pre(parent(order[i])); two gathers and a coalesced write (a
+// scatter to pre(v) would cost a read-for-fill and a write-back per random sector). The root is
+// never inside a query range.
+__global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *__restrict__ pre,
+                             const int32_t *__restrict__ order, int32_t n, int32_t *__restrict__ q0) {
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        const int32_t v = order[i];
+        const int32_t p = (v >= 0 && v < n) ? parent[v] : -1;
+        q0[i] = (p >= 0 && p < n) ? __ldg(pre + p) : -1;
     }
 }
 
@@ -305,14 +309,14 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
     h->ld = sparse_ld(n);
     h->blocked = rmq_params().blocked;
     h->bl = blocked_layout(n, max_n);
-    const size_t table_entries = h->blocked ? size_t(h->bl.elems()) : size_t(h->ld) * size_t(h->levels);
+    const size_t table_bytes = (h->blocked ? size_t(h->bl.elems()) : size_t(h->ld) * size_t(h->levels)) * 4;
     const size_t nb = size_t(n) * sizeof(int32_t);
     bool ok = dev_alloc((void **)&h->pre, nb, s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->depth, nb, s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->size, nb, s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->order, nb, s) == cudaSuccess;
     if (with_table)
-        ok = ok && dev_alloc((void **)&h->table, table_entries * sizeof(int32_t), s) == cudaSuccess;
+        ok = ok && dev_alloc((void **)&h->table, table_bytes, s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->status, sizeof(int32_t), s) == cudaSuccess;
     if (ok && batch)
         ok = dev_alloc((void **)&h->node_off, size_t(k + 1) * sizeof(int32_t), s) == cudaSuccess;
@@ -384,7 +388,7 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
         }
         if (!st && with_table) {
             PhaseTimer pt("lca.parent_pre", s);
-            k_parent_pre<<<grid_for(n, 256), 256, 0, s>>>(par, h->pre, n, h->table);
+            k_parent_pre<<<grid_for(n, 256), 256, 0, s>>>(par, h->pre, h->order, n, h->table);
             note_launch();
             st = last_launch();
         }

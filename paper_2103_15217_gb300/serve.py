@@ -89,8 +89,8 @@ class _Batch:
 
 def resident_bytes(sizes, blocked: bool = True) -> int:
     """Device bytes of a resident batch handle over trees of these sizes: pre, depth, size, order and
-    the range-minimum table (blocked: three arrays of n plus a sparse table over blocks of 32;
-    full: one row of n per level)."""
+    the range-minimum table (blocked: three int32 arrays of n plus a sparse table over blocks of 32;
+    full: one int32 row of n per level)."""
     n = int(sum(sizes))
     if blocked:
         nblk = (n + 31) // 32
