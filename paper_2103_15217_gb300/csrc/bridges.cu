@@ -25,7 +25,7 @@
 // Phase 4, the test: forest edge {u, parent(u)} is a bridge iff
 //   low(u) >= tin(u) and high(u) <= tout(u), i.e. no non-forest edge leaves
 //   the subtree of u. (Sec. 4.1 states the condition the other way round;
-//   "at least one of low, high outside the subtree" is the NON-bridge case,
+//   low or high escaping the subtree's interval is the NON-bridge case,
 //   since such an edge reconnects the subtree with the rest of the graph.)
 #include <climits>
 
