@@ -686,8 +686,17 @@ def compare_methods(parent_np, u_np, v_np, dev, naive_step_budget=2e9):
     def pre_inl():
         x = etl.lca_preprocess(P, methods=("inlabel",))
         x.free()
+
+    def pre_tour():
+        x = etl.lca_preprocess(P, methods=("tour_rmq",))
+        x.free()
     t_rmq_pre = _median_ms(pre_rmq)
     t_inl_pre = _median_ms(pre_inl)
+    t_tour_pre = _median_ms(pre_tour)
+    ht = etl.lca_preprocess(P, methods=("tour_rmq",))
+    out_t = torch.empty_like(U)
+    t_tour_q = _median_ms(lambda: ht.query_tour(U, V, out=out_t))
+    ht.free()
     out_r = torch.empty_like(U)
     out_i = torch.empty_like(U)
     t_rmq_q = _median_ms(lambda: h.query(U, V, out=out_r))
@@ -710,13 +719,15 @@ def compare_methods(parent_np, u_np, v_np, dev, naive_step_budget=2e9):
         hf.free()
     finally:
         etl.tune_set(rmq_blocked=blocked0)
-    agree = bool(torch.equal(out_r, out_i) and torch.equal(out_r[:qn], out_n) and torch.equal(out_r, out_f))
+    agree = bool(torch.equal(out_r, out_i) and torch.equal(out_r[:qn], out_n) and torch.equal(out_r, out_f)
+                 and torch.equal(out_r, out_t))
     h.free()
     res.update({
         "avg_depth": depth_mean,
         "rmq": {"preprocess_ms": t_rmq_pre, "query_ms": t_rmq_q, "queries_per_s": q / t_rmq_q * 1e3,
                 "table": "blocked" if blocked0 else "full"},
         "rmq_full_table": {"preprocess_ms": t_full_pre, "query_ms": t_full_q, "queries_per_s": q / t_full_q * 1e3},
+        "rmq_euler_tour": {"preprocess_ms": t_tour_pre, "query_ms": t_tour_q, "queries_per_s": q / t_tour_q * 1e3},
         "inlabel": {"preprocess_ms": t_inl_pre, "query_ms": t_inl_q, "queries_per_s": q / t_inl_q * 1e3},
         "naive": {"preprocess_ms": t_nv_pre, "queries_timed": qn, "query_ms_for_timed": t_nv_q,
                   "queries_per_s": qn / t_nv_q * 1e3, "query_ms_for_all_q_est": t_nv_q * q / qn},
@@ -774,7 +785,93 @@ def run_methods(args, dev, trees=None):
         u, v = synth.lca_queries(n, n, seed=3)
         g = "inf" if grasp is None else str(grasp)
         out[f"grasp_{g}"] = compare_methods(parent, u, v, dev)
+    out["queries_to_nodes"] = queries_to_nodes(n, dev)
+    out["batch_size"] = batch_size_sweep(n, dev, small=args.small)
     return out
+
+
+def queries_to_nodes(n, dev):
+    """Total time (preprocessing + all queries) against the queries-to-nodes ratio on a shallow tree
+    (the experiment of Sec. 3.3, "Queries to Nodes Ratio"): RMQ, Inlabel and the naive method."""
+    import torch
+
+    import paper_2103_15217_gb300 as etl
+    import synth
+    P = torch.from_numpy(synth.tree_parent(n, None, seed=4)).to(dev)
+    qmax = 16 * n
+    u, v = synth.lca_queries(n, qmax, seed=4)
+    U, V = torch.from_numpy(u).to(dev), torch.from_numpy(v).to(dev)
+    out_r = torch.empty_like(U)
+    out_i = torch.empty_like(U)
+    out_n = torch.empty_like(U)
+    res = {"n": n, "tree": "random recursive (shallow)", "rows": []}
+    agree = True
+    for ratio in (0.125, 0.25, 0.5, 1, 2, 4, 8, 16):
+        q = int(n * ratio)
+
+        def rmq():
+            h = etl.lca_preprocess(P)
+            h.query(U[:q], V[:q], out=out_r[:q])
+            h.free()
+
+        def inl():
+            h = etl.lca_preprocess(P, methods=("inlabel",))
+            h.query_inlabel(U[:q], V[:q], out=out_i[:q])
+            h.free()
+
+        def naive():
+            etl.NaiveLca(P).query(U[:q], V[:q], out=out_n[:q])
+        rmq(), inl(), naive()
+        torch.cuda.synchronize()
+        agree = agree and bool(torch.equal(out_r[:q], out_i[:q]) and torch.equal(out_r[:q], out_n[:q]))
+        res["rows"].append({"queries_per_node": ratio, "q": q, "rmq_ms": _median_ms(rmq), "inlabel_ms": _median_ms(inl),
+                            "naive_ms": _median_ms(naive)})
+    res["answers_identical"] = agree
+    return res
+
+
+def batch_size_sweep(n, dev, small=False):
+    """Queries answered in batches of a given size, one launch per batch, on one preprocessed shallow
+    tree (the experiment of Sec. 3.3, "Batch Size"): query throughput against batch size."""
+    import torch
+
+    import paper_2103_15217_gb300 as etl
+    import synth
+    P = torch.from_numpy(synth.tree_parent(n, None, seed=5)).to(dev)
+    q = n
+    u, v = synth.lca_queries(n, q, seed=5)
+    U, V = torch.from_numpy(u).to(dev), torch.from_numpy(v).to(dev)
+    h = etl.lca_preprocess(P, methods=("rmq", "inlabel"))
+    out_r = torch.empty_like(U)
+    out_i = torch.empty_like(U)
+    ref = h.query(U, V)
+    rows = []
+    agree = True
+    for lb in range(8 if small else 10, int(np.log2(q)) + 1, 2):
+        b = 1 << lb
+
+        def run(fn, out):
+            for s in range(0, q, b):
+                fn(U[s:s + b], V[s:s + b], out=out[s:s + b])
+        t_r = _median_ms(lambda: run(h.query, out_r))
+        t_i = _median_ms(lambda: run(h.query_inlabel, out_i))
+        agree = agree and bool(torch.equal(out_r, ref) and torch.equal(out_i, ref))
+        # the same launches captured once as a CUDA graph: no host work per batch
+        out_r.zero_()
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=cs):
+            run(h.query, out_r)
+        torch.cuda.synchronize()
+        t_g = _median_ms(g.replay)
+        agree = agree and bool(torch.equal(out_r, ref))
+        del g
+        rows.append({"batch": b, "launches": (q + b - 1) // b, "rmq_ms": t_r, "rmq_queries_per_s": q / t_r * 1e3,
+                     "inlabel_ms": t_i, "inlabel_queries_per_s": q / t_i * 1e3,
+                     "rmq_graph_ms": t_g, "rmq_graph_queries_per_s": q / t_g * 1e3})
+    h.free()
+    return {"n": n, "q": q, "rows": rows, "answers_identical": agree}
 
 
 # ------------------------------------------------------------------ serving

@@ -117,9 +117,12 @@ etl_status lca_preprocess(const int32_t *parent, int32_t n, void *stream, etl_lc
  * lca_preprocess_ex: as lca_preprocess, choosing which query structures to
  * build: ETL_LCA_RMQ (the range-minimum table, for lca_query) and/or
  * ETL_LCA_INLABEL (the Inlabel records, for lca_query_inlabel; the paper's
- * GPU method, O(n) memory). Unknown bits or neither bit: ETL_EINVAL.
+ * GPU method, O(n) memory) and/or ETL_LCA_TOUR_RMQ (range minimum over the
+ * depth-annotated Euler tour, the classical LCA-to-RMQ reduction of Sec. 3.1,
+ * for lca_query_tour: a blocked table of 64-bit keys over 2n tour positions).
+ * Unknown bits or no bit: ETL_EINVAL.
  */
-enum { ETL_LCA_RMQ = 1, ETL_LCA_INLABEL = 2 };
+enum { ETL_LCA_RMQ = 1, ETL_LCA_INLABEL = 2, ETL_LCA_TOUR_RMQ = 4 };
 etl_status lca_preprocess_ex(const int32_t *parent, int32_t n, int32_t flags, void *stream, etl_lca_t *out);
 
 /*
@@ -177,6 +180,18 @@ etl_status lca_query_batch(etl_lca_t h, const int32_t *inst, const int32_t *u, c
 etl_status lca_build_inlabel(etl_lca_t h, const int32_t *parent, void *stream);
 etl_status lca_query_inlabel(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q, int32_t *out,
                              int32_t *status, void *stream);
+
+/*
+ * lca_query_tour: out[i] = LCA(u[i], v[i]) by range minimum over the Euler
+ * tour (Sec. 3.1): entry r of the tour holds depth << 32 | node of the node
+ * the tour is at after bracket r, and the minimum over the positions of the
+ * two opening brackets names the LCA. Same results and error rules as
+ * lca_query; the handle must come from lca_preprocess_ex with
+ * ETL_LCA_TOUR_RMQ (ETL_EINVAL otherwise, and for batch handles). Arrays are
+ * device pointers owned by the caller, enqueued on `stream`.
+ */
+etl_status lca_query_tour(etl_lca_t h, const int32_t *u, const int32_t *v, int64_t q, int32_t *out,
+                          int32_t *status, void *stream);
 
 /*
  * The naive GPU LCA the paper compares against (Sec. 3.1, "The Naive

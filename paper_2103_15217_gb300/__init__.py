@@ -27,7 +27,7 @@ STATUS = {0: "ETL_OK", 1: "ETL_EINVAL", 2: "ETL_ENOMEM", 3: "ETL_ECUDA", 4: "ETL
           5: "ETL_EBADQUERY", 6: "ETL_EBADGRAPH", 7: "ETL_ETIMEOUT"}
 EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_preprocess", "lca_query", "lca_status", "lca_arrays",
            "lca_export", "lca_free", "find_bridges", "lca_preprocess_batch", "lca_query_batch", "find_bridges_batch",
-           "lca_build_inlabel", "lca_query_inlabel", "lca_naive_preprocess", "lca_naive_query",
+           "lca_build_inlabel", "lca_query_inlabel", "lca_query_tour", "lca_naive_preprocess", "lca_naive_query",
            "lca_preprocess_ex", "etl_trim", "two_edge_cc", "find_bridges_hybrid", "etl_profile_enable", "etl_profile_reset",
            "etl_profile_count", "etl_profile_get", "etl_launch_count", "etl_tune_set", "etl_tune_get")
 TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
@@ -82,6 +82,7 @@ def load_library(path: str | None = None):
         lib.lca_naive_preprocess.argtypes = [P, i32, P, P, P]
         lib.lca_naive_query.argtypes = [P, i32, P, P, i64, P, P, P]
         lib.lca_query_inlabel.argtypes = [P, P, P, i64, P, P, P]
+        lib.lca_query_tour.argtypes = [P, P, P, i64, P, P, P]
         lib.lca_query_batch.argtypes = [P, P, P, P, i64, P, P, P]
         lib.find_bridges_batch.argtypes = [P, P, P, i32, i64, i32, P, P, P]
         lib.etl_launch_count.argtypes = [ctypes.POINTER(i64)]
@@ -153,7 +154,11 @@ class Lca:
                 int(max_n if max_n is not None else self.n), self._stream, ctypes.byref(self._h)))
         else:
             self.k = 1
-            flags = (1 if "rmq" in methods else 0) | (2 if "inlabel" in methods else 0)
+            unknown = set(methods) - {"rmq", "inlabel", "tour_rmq"}
+            if unknown:
+                raise ValueError(f"unknown LCA methods {sorted(unknown)}")
+            flags = (1 if "rmq" in methods else 0) | (2 if "inlabel" in methods else 0) | \
+                (4 if "tour_rmq" in methods else 0)
             _check("lca_preprocess_ex", lib.lca_preprocess_ex(_dev_i32(parent, "parent"), self.n, flags,
                                                               self._stream, ctypes.byref(self._h)))
         self._refs = (parent, node_off)  # keep the inputs alive until preprocessing has run
@@ -196,6 +201,17 @@ class Lca:
         _check("lca_query_inlabel", self._lib.lca_query_inlabel(self._h, _dev_i32(u, "u"), _dev_i32(v, "v"), u.numel(),
                                                                 _dev_i32(out, "out"), _status_ptr(status),
                                                                 _stream(stream)))
+        return out
+
+    def query_tour(self, u: torch.Tensor, v: torch.Tensor, out: torch.Tensor | None = None,
+                   status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """LCA by range minimum over the Euler tour (needs methods including "tour_rmq")."""
+        if u.numel() != v.numel():
+            raise ValueError("u and v must have the same length")
+        if out is None:
+            out = torch.empty_like(u)
+        _check("lca_query_tour", self._lib.lca_query_tour(self._h, _dev_i32(u, "u"), _dev_i32(v, "v"), u.numel(),
+                                                          _dev_i32(out, "out"), _status_ptr(status), _stream(stream)))
         return out
 
     def status(self) -> int:
@@ -272,7 +288,8 @@ def profile_read() -> dict:
 
 
 def lca_preprocess(parent: torch.Tensor, stream=None, methods: tuple = ("rmq",)) -> Lca:
-    """Preprocess one tree; methods: any of "rmq" (lca query) and "inlabel" (query_inlabel)."""
+    """Preprocess one tree; methods: any of "rmq" (query), "inlabel" (query_inlabel) and "tour_rmq"
+    (query_tour)."""
     return Lca(parent, stream, methods=methods)
 
 

@@ -219,6 +219,11 @@ struct OpMax {
     __device__ static __forceinline__ T id() { return INT32_MIN; }
     __device__ static __forceinline__ T f(T a, T b) { return max(a, b); }
 };
+struct OpMinKey {  // 64-bit keys: a value in the high half, a payload it carries in the low half
+    using T = long long;
+    __device__ static __forceinline__ T id() { return INT64_MAX; }
+    __device__ static __forceinline__ T f(T a, T b) { return min(a, b); }
+};
 struct OpMinMax {  // x = min of the first component, y = max of the second
     using T = int2;
     __device__ static __forceinline__ T id() { return make_int2(INT32_MAX, INT32_MIN); }
@@ -291,4 +296,7 @@ struct etl_lca_s {
     bool has_table = false;     // RMQ sparse table built (lca_query available)
     void *inrec = nullptr;      // Inlabel: per node (inlabel, ascendant, depth, parent), int4[n]
     void *inpath = nullptr;     // Inlabel: per inlabel value (parent of the path head, its depth), int2[n+1]
+    void *tour_table = nullptr;  // Euler-tour RMQ: blocked table of (depth << 32 | node) keys over 2n positions
+    int32_t *tpos = nullptr;     // Euler-tour RMQ: tour position of each node's opening bracket
+    etl::BlockedLayout tbl{};
 };

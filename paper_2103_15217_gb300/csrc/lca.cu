@@ -291,7 +291,7 @@ void free_handle(etl_lca_s *h) {
     cudaStream_t s = h->stream;
     for (int32_t *p : {h->pre, h->depth, h->size, h->order, h->table, h->status, h->node_off})
         if (p) cudaFreeAsync(p, s);
-    for (void *p : {h->inrec, h->inpath})
+    for (void *p : {h->inrec, h->inpath, h->tour_table, static_cast<void *>(h->tpos)})
         if (p) cudaFreeAsync(p, s);
     delete h;
 }
@@ -440,22 +440,21 @@ extern "C" etl_status lca_preprocess(const int32_t *parent, int32_t n, void *str
 }
 
 etl_status lca_build_inlabel_impl(etl_lca_t h, const int32_t *parent, cudaStream_t s);
+etl_status lca_build_tour_impl(etl_lca_t h, const int32_t *parent, cudaStream_t s);
 
 extern "C" etl_status lca_preprocess_ex(const int32_t *parent, int32_t n, int32_t flags, void *stream,
                                         etl_lca_t *out) {
     if (!out) return ETL_EINVAL;
     *out = nullptr;
-    if (!parent || n < 1 || n > (1 << 30) - 1 || !(flags & (ETL_LCA_RMQ | ETL_LCA_INLABEL)) ||
-        (flags & ~(ETL_LCA_RMQ | ETL_LCA_INLABEL)))
-        return ETL_EINVAL;
+    constexpr int32_t kAll = ETL_LCA_RMQ | ETL_LCA_INLABEL | ETL_LCA_TOUR_RMQ;
+    if (!parent || n < 1 || n > (1 << 30) - 1 || !(flags & kAll) || (flags & ~kAll)) return ETL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     etl_status st = lca_build(parent, n, nullptr, 1, n, (flags & ETL_LCA_RMQ) != 0, s, out);
-    if (!st && (flags & ETL_LCA_INLABEL)) {
-        st = lca_build_inlabel_impl(*out, parent, s);
-        if (st) {
-            free_handle(*out);
-            *out = nullptr;
-        }
+    if (!st && (flags & ETL_LCA_INLABEL)) st = lca_build_inlabel_impl(*out, parent, s);
+    if (!st && (flags & ETL_LCA_TOUR_RMQ)) st = lca_build_tour_impl(*out, parent, s);
+    if (st && *out) {
+        free_handle(*out);
+        *out = nullptr;
     }
     return st;
 }

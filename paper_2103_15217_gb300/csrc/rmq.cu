@@ -82,7 +82,9 @@ __device__ __forceinline__ int32_t shfl_up(int32_t v, int d) { return __shfl_up_
 __device__ __forceinline__ int2 shfl_up(int2 v, int d) {
     return make_int2(__shfl_up_sync(kFull, v.x, d), __shfl_up_sync(kFull, v.y, d));
 }
+__device__ __forceinline__ long long shfl_up(long long v, int d) { return __shfl_up_sync(kFull, v, d); }
 __device__ __forceinline__ int32_t shfl_down(int32_t v, int d) { return __shfl_down_sync(kFull, v, d); }
+__device__ __forceinline__ long long shfl_down(long long v, int d) { return __shfl_down_sync(kFull, v, d); }
 __device__ __forceinline__ int2 shfl_down(int2 v, int d) {
     return make_int2(__shfl_down_sync(kFull, v.x, d), __shfl_down_sync(kFull, v.y, d));
 }
@@ -174,6 +176,7 @@ etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L
 template etl_status blocked_build<OpMin>(int32_t *, int64_t, const BlockedLayout &, cudaStream_t);
 template etl_status blocked_build<OpMax>(int32_t *, int64_t, const BlockedLayout &, cudaStream_t);
 template etl_status blocked_build<OpMinMax>(int2 *, int64_t, const BlockedLayout &, cudaStream_t);
+template etl_status blocked_build<OpMinKey>(long long *, int64_t, const BlockedLayout &, cudaStream_t);
 
 RmqParams &rmq_params() {
     static RmqParams p;
