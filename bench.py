@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", choices=["all", "core", "batched", "serve", "methods"], default="all",
                     help="core = the scale workload; batched = 4096 mixed instances, batched vs per-instance")
-    ap.add_argument("--case", choices=["lca", "easy", "hard"], default=None,
+    ap.add_argument("--case", choices=["lca", "easy", "hard", "batch_trees", "batch_graphs"], default=None,
                     help="run one workload of size --n twice (warm-up + one more) and exit; for profilers")
     ap.add_argument("--n", type=int, default=1 << 22)
     ap.add_argument("--grasp", type=int, default=0, help="tree grasp for --case lca (0 = unlimited)")
@@ -596,11 +596,24 @@ def run_batched(args, dev):
     defaults = etl.tune_get()
     tuned = tune.autotune(n=int(min(1 << 23, max(1 << 16, int(B["toff"][-1])))), use_cache=False)
 
-    def batched():
+    side = torch.cuda.Stream()
+
+    def batched_trees():
         h = etl.lca_preprocess_batch(P, O, max_n)
         h.query_batch(I, U, V, out=out_b)
         h.free()
+
+    def batched_graphs():
         mask_b.copy_(etl.find_bridges_batch(E, EO, NO, total_gn))
+
+    def batched():
+        """The tree batch and the graph batch are independent: the graphs run on a forked stream."""
+        main = torch.cuda.current_stream()
+        side.wait_stream(main)
+        batched_trees()
+        with torch.cuda.stream(side):
+            batched_graphs()
+        main.wait_stream(side)
 
     def timed(fn, reps, graph=None):
         ts = []
@@ -635,6 +648,16 @@ def run_batched(args, dev):
     g.replay()
     torch.cuda.synchronize()
     equal = equal and bool(torch.equal(torch.cat(outs_pi), out_b) and torch.equal(torch.cat(masks_pi), mask_b))
+    del g
+    parts = {}
+    for name, fn in (("trees", batched_trees), ("graphs", batched_graphs)):
+        gp = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gp, stream=stream):
+            fn()
+        gp.replay()
+        torch.cuda.synchronize()
+        parts[name + "_ms"] = timed(None, args.steps, graph=gp) * 1e3
+        del gp
     etl.tune_set(**defaults)
     return {
         "autotuned": {"params": tuned["params"], "sample_ms": tuned["ms"], "default_ms": tuned["default_ms"],
@@ -643,7 +666,9 @@ def run_batched(args, dev):
                      f" + {len(ge)} graphs n log-uniform 2^6..2^16, m = 4n (easy/hard alternating)"),
         "queries": q_total, "edges": m_total, "tree_nodes": int(B["toff"][-1]), "graph_nodes": total_gn,
         "per_instance": {"ms": t_pi * 1e3, "value": units / t_pi},
-        "batched_graph": {"ms": t_b * 1e3, "value": units / t_b, "captured": True},
+        "batched_graph": {"ms": t_b * 1e3, "value": units / t_b, "captured": True,
+                          "concurrency": "tree batch and graph batch on two parallel graph branches",
+                          "alone": parts},
         "speedup": t_pi / t_b, "results_identical": equal, "unit": UNIT,
         "host_launch_sites_during_replay": launches_b,
     }
@@ -1000,6 +1025,19 @@ def run_case(args):
     etl.build()
     dev = torch.device("cuda", 0)
     n = args.n
+    if args.case in ("batch_trees", "batch_graphs"):
+        B = make_batch_inputs(small=False)
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+        for _ in range(2):
+            if args.case == "batch_trees":
+                h = etl.lca_preprocess_batch(T(np.concatenate(B["tp"])), T(B["toff"]), max(d["n"] for d in B["trees"]))
+                h.query_batch(T(np.concatenate(B["ti"])), T(np.concatenate(B["tu"])), T(np.concatenate(B["tv"])))
+                h.free()
+            else:
+                etl.find_bridges_batch(T(np.concatenate(B["ge"])), T(B["eoff"]), T(B["noff"]), int(B["noff"][-1]))
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "launches": etl.launch_count()}))
+        return
     if args.case == "lca":
         parent = torch.from_numpy(synth.tree_parent(n, args.grasp or None, seed=1)).to(dev)
         u, v = (torch.from_numpy(x).to(dev) for x in synth.lca_queries(n, n, seed=1))
