@@ -278,6 +278,9 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  *                           O(n) memory); 0: full sparse tables (n log n
  *                           entries). Both answer every query exactly. (1)
  *                           Read when a handle or a bridge call is built.
+ *   ETL_TUNE_SORT_ROUNDS    32-element rounds per warp in the radix-sort
+ *                           passes that group children by parent: tiles of
+ *                           256 * value elements, value 8 or 16 (8)
  * Unknown keys or out-of-range values return ETL_EINVAL.
  */
 enum {
@@ -288,7 +291,8 @@ enum {
     ETL_TUNE_RMQ_LEVELS_PER_PASS = 5,
     ETL_TUNE_RMQ_BLOCK = 6,
     ETL_TUNE_CC_FIRST_SLICE = 7,
-    ETL_TUNE_RMQ_BLOCKED = 8
+    ETL_TUNE_RMQ_BLOCKED = 8,
+    ETL_TUNE_SORT_ROUNDS = 9
 };
 etl_status etl_tune_set(int32_t key, int32_t value);
 etl_status etl_tune_get(int32_t key, int32_t *value);

@@ -126,6 +126,10 @@ extern "C" etl_status etl_tune_set(int32_t key, int32_t value) {
             if (value != 0 && value != 1) return ETL_EINVAL;
             rmq_params().blocked = value != 0;
             return ETL_OK;
+        case ETL_TUNE_SORT_ROUNDS:
+            if (value != 8 && value != 16) return ETL_EINVAL;
+            sort_params().rounds = value;
+            return ETL_OK;
         default:
             return ETL_EINVAL;
     }
@@ -143,6 +147,7 @@ extern "C" etl_status etl_tune_get(int32_t key, int32_t *value) {
         case ETL_TUNE_RMQ_BLOCK: *value = rmq_params().block; return ETL_OK;
         case ETL_TUNE_CC_FIRST_SLICE: *value = cc_params().first_slice_quarters; return ETL_OK;
         case ETL_TUNE_RMQ_BLOCKED: *value = rmq_params().blocked ? 1 : 0; return ETL_OK;
+        case ETL_TUNE_SORT_ROUNDS: *value = sort_params().rounds; return ETL_OK;
         default: return ETL_EINVAL;
     }
 }

@@ -146,6 +146,11 @@ struct RankParams {
 };
 RankParams &rank_params();
 
+struct SortParams {
+    int rounds = 8;  // 32-element rounds per warp in the radix passes: tiles of 256 * rounds elements
+};
+SortParams &sort_params();
+
 struct CcParams {
     int first_slice_quarters = 4;  // edges hooked before the first compression, in units of n/4
 };

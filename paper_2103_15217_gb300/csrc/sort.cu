@@ -17,10 +17,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / kWarp;
-constexpr int kRounds = 8;                      // 32-element rounds per warp
-constexpr int kWarpTile = kWarp * kRounds;      // 256
-constexpr int kTile = kWarps * kWarpTile;       // 2048 elements per block
 constexpr int kRadix = 256;
+// R = 32-element rounds per warp: a tile of 8 warps holds 256 * R elements (R = 8 or 16, chosen by
+// the SORT_ROUNDS tuning knob; larger tiles give longer runs per digit in the scatter)
 
 __device__ __forceinline__ int64_t count_of(const int32_t *d_count, int64_t n_cap) {
     if (!d_count) return n_cap;
@@ -33,9 +32,11 @@ __device__ __forceinline__ int32_t key_at(const int32_t *keys, const int2 *kv, i
     return kv ? kv[i].x : keys[i];
 }
 
+template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_hist(const int32_t *__restrict__ keys, const int2 *__restrict__ kv, const int32_t *d_count, int64_t n_cap,
            int shift, int32_t key_limit, int32_t *__restrict__ ghist, int nblocks) {
+    constexpr int kRounds = R, kWarpTile = kWarp * R, kTile = kWarps * kWarpTile;
     __shared__ int32_t h[kRadix];
     const int64_t count = count_of(d_count, n_cap);
     if (int64_t(blockIdx.x) * kTile >= count) {  // tile past the data: an all-zero histogram
@@ -46,22 +47,27 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kTile + warp * kWarpTile;
+    int32_t key[kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {  // loads first, all in flight together
+        const int64_t idx = base + r * kWarp + lane;
+        key[r] = idx < count ? key_at(keys, kv, idx) : -1;
+    }
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-        int64_t idx = base + r * kWarp + lane;
-        if (idx < count) {
-            int32_t k = key_at(keys, kv, idx);
-            if (k >= 0 && k < key_limit) atomicAdd(&h[(k >> shift) & (kRadix - 1)], 1);
-        }
+        const int32_t k = key[r];
+        if (k >= 0 && k < key_limit) atomicAdd(&h[(k >> shift) & (kRadix - 1)], 1);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kThreads) ghist[int64_t(d) * nblocks + blockIdx.x] = h[d];
 }
 
+template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, const int2 *__restrict__ kv,
               const int32_t *d_count, int64_t n_cap, int shift, int32_t key_limit, const int32_t *__restrict__ goff,
               int nblocks, int2 *__restrict__ kv_out) {
+    constexpr int kRounds = R, kWarpTile = kWarp * R, kTile = kWarps * kWarpTile;
     __shared__ int32_t wcnt[kWarps][kRadix];
     __shared__ int32_t gbase[kRadix];
     const int64_t count = count_of(d_count, n_cap);
@@ -71,23 +77,28 @@ __global__ void __launch_bounds__(kThreads)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kTile + warp * kWarpTile;
     int32_t key[kRounds], val[kRounds], dig[kRounds], lrank[kRounds];
+    // all loads of the tile first, so that they are in flight together (the ranking rounds below
+    // are ordered by __syncwarp and would otherwise wait for one load each)
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-        int64_t idx = base + r * kWarp + lane;
-        bool valid = false;
-        int32_t k = -1;
-        int32_t v = 0;
+        const int64_t idx = base + r * kWarp + lane;
+        key[r] = -1;
+        val[r] = 0;
         if (idx < count) {
             if (kv) {
-                const int2 x = kv[idx];
-                k = x.x;
-                v = x.y;
+                const int2 x = __ldcs(kv + idx);
+                key[r] = x.x;
+                val[r] = x.y;
             } else {
-                k = keys[idx];
-                v = vals ? vals[idx] : int32_t(idx);
+                key[r] = __ldcs(keys + idx);
+                val[r] = vals ? __ldcs(vals + idx) : int32_t(idx);
             }
-            valid = (k >= 0 && k < key_limit);
         }
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int32_t k = key[r];
+        const bool valid = k >= 0 && k < key_limit;  // also false past the end (k = -1)
         int d = valid ? ((k >> shift) & (kRadix - 1)) : (kRadix + lane);  // invalid lanes get unique dummies
         unsigned peers = __match_any_sync(kFull, d);
         int pre = 0;
@@ -95,8 +106,6 @@ __global__ void __launch_bounds__(kThreads)
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = pre + __popc(peers);
         __syncwarp();
-        key[r] = k;
-        val[r] = v;
         dig[r] = valid ? d : -1;
         lrank[r] = pre + __popc(peers & lanemask_lt());
     }
@@ -121,10 +130,10 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-}  // namespace
-
-etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, const int32_t *d_count, int64_t n_cap,
-                            int key_bits, int32_t key_limit, Workspace &ws, SortResult *out) {
+template <int R>
+etl_status radix_sort_impl(const int32_t *keys_in, const int32_t *vals_in, const int32_t *d_count, int64_t n_cap,
+                           int key_bits, int32_t key_limit, Workspace &ws, SortResult *out) {
+    constexpr int kTile = kWarps * kWarp * R;
     cudaStream_t s = ws.stream();
     const int64_t cap = n_cap > 0 ? n_cap : 1;
     const int nblocks = int(ceil_div(cap, kTile));
@@ -142,8 +151,8 @@ etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, cons
         etl_status st;
         {
             PhaseTimer pt("sort.hist", s);
-            k_hist<<<nblocks, kThreads, 0, s>>>(keys_in, kvin, cnt, cap, shift, key_limit, ghist, nblocks);
-        note_launch();
+            k_hist<R><<<nblocks, kThreads, 0, s>>>(keys_in, kvin, cnt, cap, shift, key_limit, ghist, nblocks);
+            note_launch();
             st = last_launch();
         }
         if (st) return st;
@@ -152,9 +161,9 @@ etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, cons
         int2 *out_kv = buf[p & 1];
         {
             PhaseTimer pt("sort.scatter", s);
-            k_scatter<<<nblocks, kThreads, 0, s>>>(keys_in, vals_in, kvin, cnt, cap, shift, key_limit, goff, nblocks,
-                                                   out_kv);
-        note_launch();
+            k_scatter<R><<<nblocks, kThreads, 0, s>>>(keys_in, vals_in, kvin, cnt, cap, shift, key_limit, goff,
+                                                      nblocks, out_kv);
+            note_launch();
             st = last_launch();
         }
         if (st) return st;
@@ -164,6 +173,20 @@ etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, cons
     out->kv = kvin;
     out->d_total = cnt;
     return ETL_OK;
+}
+
+}  // namespace
+
+SortParams &sort_params() {
+    static SortParams p;
+    return p;
+}
+
+etl_status radix_sort_pairs(const int32_t *keys_in, const int32_t *vals_in, const int32_t *d_count, int64_t n_cap,
+                            int key_bits, int32_t key_limit, Workspace &ws, SortResult *out) {
+    if (sort_params().rounds == 16)
+        return radix_sort_impl<16>(keys_in, vals_in, d_count, n_cap, key_bits, key_limit, ws, out);
+    return radix_sort_impl<8>(keys_in, vals_in, d_count, n_cap, key_bits, key_limit, ws, out);
 }
 
 }  // namespace etl

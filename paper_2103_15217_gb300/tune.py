@@ -36,6 +36,7 @@ SPACE = [
     ("rmq_block", [256, 512]),
     ("cc_first_slice", [2, 8, 16]),
     ("rmq_blocked", [0, 1]),
+    ("sort_rounds", [8, 16]),
 ]
 
 
