@@ -271,7 +271,8 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  *                           128, 256, 512 or 1024 (256)
  *   ETL_TUNE_CC_FIRST_SLICE edges hooked before the first compression of the
  *                           connected-components pass, in units of n/4,
- *                           1..64 (4, i.e. n edges)
+ *                           1..64 (2, i.e. n/2 edges: a random sample of that
+ *                           size is still below the giant-component threshold)
  *   ETL_TUNE_RMQ_BLOCKED    1: range-min / max tables are blocked two-level
  *                           tables (prefix / suffix results inside blocks of
  *                           32 entries plus a sparse table over the blocks,
@@ -281,6 +282,14 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  *   ETL_TUNE_SORT_ROUNDS    32-element rounds per warp in the radix-sort
  *                           passes that group children by parent: tiles of
  *                           256 * value elements, value 8 or 16 (8)
+ *   ETL_TUNE_CC_DOUBLING    1: after the first slice the connected-components
+ *                           pass hooks the edges in slices that double in
+ *                           size, compressing the forest before each; 0: the
+ *                           rest in one launch (0)
+ *   ETL_TUNE_CC_GIANT       1: after each compression the most frequent root
+ *                           of a sample (the giant component's) outranks all
+ *                           others when roots are hooked, so it never moves;
+ *                           0: plain smaller-id order (1)
  * Unknown keys or out-of-range values return ETL_EINVAL.
  */
 enum {
@@ -292,7 +301,9 @@ enum {
     ETL_TUNE_RMQ_BLOCK = 6,
     ETL_TUNE_CC_FIRST_SLICE = 7,
     ETL_TUNE_RMQ_BLOCKED = 8,
-    ETL_TUNE_SORT_ROUNDS = 9
+    ETL_TUNE_SORT_ROUNDS = 9,
+    ETL_TUNE_CC_DOUBLING = 10,
+    ETL_TUNE_CC_GIANT = 11
 };
 etl_status etl_tune_set(int32_t key, int32_t value);
 etl_status etl_tune_get(int32_t key, int32_t *value);

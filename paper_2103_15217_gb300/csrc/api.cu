@@ -43,6 +43,10 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
             if (cudaMemPoolCreate(&np, &props) != cudaSuccess) return cudaMallocAsync(p, bytes, s);
             uint64_t keep = UINT64_MAX;
             cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            // never make a stream wait on another one to reuse a block freed there: independent
+            // calls on different streams must not be serialised by the allocator
+            int no = 0;
+            cudaMemPoolSetAttribute(np, cudaMemPoolReuseAllowInternalDependencies, &no);
             g_pool[dev] = np;
         }
         pool = g_pool[dev];
@@ -130,6 +134,14 @@ extern "C" etl_status etl_tune_set(int32_t key, int32_t value) {
             if (value != 8 && value != 16) return ETL_EINVAL;
             sort_params().rounds = value;
             return ETL_OK;
+        case ETL_TUNE_CC_DOUBLING:
+            if (value != 0 && value != 1) return ETL_EINVAL;
+            cc_params().doubling = value != 0;
+            return ETL_OK;
+        case ETL_TUNE_CC_GIANT:
+            if (value != 0 && value != 1) return ETL_EINVAL;
+            cc_params().giant = value != 0;
+            return ETL_OK;
         default:
             return ETL_EINVAL;
     }
@@ -148,6 +160,8 @@ extern "C" etl_status etl_tune_get(int32_t key, int32_t *value) {
         case ETL_TUNE_CC_FIRST_SLICE: *value = cc_params().first_slice_quarters; return ETL_OK;
         case ETL_TUNE_RMQ_BLOCKED: *value = rmq_params().blocked ? 1 : 0; return ETL_OK;
         case ETL_TUNE_SORT_ROUNDS: *value = sort_params().rounds; return ETL_OK;
+        case ETL_TUNE_CC_DOUBLING: *value = cc_params().doubling ? 1 : 0; return ETL_OK;
+        case ETL_TUNE_CC_GIANT: *value = cc_params().giant ? 1 : 0; return ETL_OK;
         default: return ETL_EINVAL;
     }
 }

@@ -51,7 +51,7 @@ __device__ __forceinline__ int32_t find_root(int32_t *par, int32_t x, int64_t &b
         if (p == x) return x;
         const int32_t gp = __ldcg(par + p);
         if (gp == p) return p;
-        par[x] = gp;  // only non-roots are rewritten, always to a smaller id
+        par[x] = gp;  // only non-roots are rewritten, always to an ancestor
         x = gp;
     }
     return -1;
@@ -80,11 +80,22 @@ __device__ __forceinline__ int64_t hook_chunk(int64_t c, int64_t nsuper, bool sp
     return spread ? ((c / kHookSuper) * kP % nsuper) * kHookSuper + c % kHookSuper : c;
 }
 
+// Roots are hooked under roots of higher priority: a smaller id, except that the root named by
+// *giant (if any: the most frequent root after a compression, i.e. the giant component's) ranks above
+// all. Priorities are a strict total order, so the forest stays acyclic, and the giant root never
+// moves: once the giant component has formed, every later hook leaves the paths of its members as
+// they are (with plain smaller-id order the giant root moves whenever a smaller one joins, and every
+// member's path grows by a step).
+__device__ __forceinline__ bool hook_above(int32_t a, int32_t b, int32_t giant) {  // a ranks above b
+    return a == giant || (b != giant && a < b);
+}
+
 // skip (may be null): edges to leave out; is_tree (may be null): 1 for edges whose hook succeeded
 __global__ void __launch_bounds__(kHookChunk)
     k_hook(const int32_t *__restrict__ edges, int64_t m, int64_t c0, int64_t c1, bool spread, int32_t n,
            int32_t *__restrict__ par, uint8_t *__restrict__ is_tree, const uint8_t *__restrict__ skip,
-           int32_t *__restrict__ status) {
+           const int32_t *__restrict__ d_giant, int32_t *__restrict__ status) {
+    const int32_t giant = d_giant ? *d_giant : -1;
     const int64_t nsuper = ((m + kHookChunk - 1) / kHookChunk + kHookSuper - 1) / kHookSuper;
     for (int64_t c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const int64_t e = hook_chunk(c, nsuper, spread) * kHookChunk + threadIdx.x;
@@ -106,7 +117,8 @@ __global__ void __launch_bounds__(kHookChunk)
                     break;
                 }
                 if (ra == rb) break;
-                const int32_t hi = max(ra, rb), lo = min(ra, rb);
+                const bool a_up = hook_above(ra, rb, giant);
+                const int32_t hi = a_up ? rb : ra, lo = a_up ? ra : rb;  // hi goes under lo
                 if (atomicCAS(par + hi, hi, lo) == hi) {
                     tree = 1;
                     break;
@@ -128,6 +140,27 @@ __global__ void k_compress(int32_t n, int32_t *__restrict__ par, int32_t *__rest
         else
             par[v] = r;
     }
+}
+
+// The most frequent root among kGiantSample vertices spread over [0, n) (one block; par must be
+// compressed, so par[v] is v's root): the giant component's root when there is one.
+constexpr int kGiantSample = 1024;
+
+__global__ void __launch_bounds__(kGiantSample) k_giant(const int32_t *__restrict__ par, int32_t n,
+                                                         int32_t *__restrict__ giant) {
+    __shared__ int32_t root[kGiantSample];
+    __shared__ unsigned long long best;
+    const int i = threadIdx.x;
+    const int32_t v = int32_t((uint64_t(i) * 2654435761u + 12345u) % uint64_t(n));
+    root[i] = __ldcg(par + v);
+    if (i == 0) best = 0;
+    __syncthreads();
+    int32_t c = 0;
+    for (int j = 0; j < kGiantSample; ++j) c += root[j] == root[i];
+    // largest count, then smallest root id: pack (count, ~root) and take the maximum
+    atomicMax(&best, (static_cast<unsigned long long>(c) << 32) | uint32_t(~uint32_t(root[i])));
+    __syncthreads();
+    if (i == 0) *giant = int32_t(~uint32_t(best & 0xffffffffu));
 }
 
 // forest edges packed in edge order: tuv[2t] = u, tuv[2t+1] = v, tedge[t] = e
@@ -485,7 +518,7 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     uint8_t *is_tree = ws.get<uint8_t>(m), *rflag = ws.get<uint8_t>(n);
     int32_t *tpos = ws.get<int32_t>(m + 1), *rpos = ws.get<int32_t>(int64_t(n) + 1), *roots = ws.get<int32_t>(n);
     int32_t *tuv = ws.get<int32_t>(A > 0 ? A : 1), *tedge = ws.get<int32_t>(n);
-    int32_t *n_arcs = ws.get<int32_t>(1), *vhead = ws.get<int32_t>(1);
+    int32_t *n_arcs = ws.get<int32_t>(1), *vhead = ws.get<int32_t>(1), *giant = ws.get<int32_t>(1);
     int32_t *succ = ws.get<int32_t>(N);
     int32_t *child = ws.get<int32_t>(n), *etin = ws.get<int32_t>(n), *etout = ws.get<int32_t>(n);
     uint8_t *tflag = ws.get<uint8_t>(n);
@@ -502,21 +535,29 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     }
     {
         // hook a first slice of the edges, compress every path to its root, then hook the rest:
-        // after the compression most finds take one step and most edges meet equal roots at once
-        const int64_t slice = int64_t(cc_params().first_slice_quarters) * n / 4;
+        // after the compression most finds take one step and most edges meet equal roots at once.
+        // With `doubling`, the rest goes in slices that double in size, each followed by a
+        // compression, so that no phase builds long paths in a fresh part of the forest.
+        const CcParams &C = cc_params();
+        const int64_t slice = int64_t(C.first_slice_quarters) * n / 4;
         const int64_t nchunks = hook_positions(m);
-        int64_t c1 = ceil_div(slice > 0 ? slice : 1, kHookChunk);
-        if (c1 > nchunks) c1 = nchunks;
+        int64_t w = ceil_div(slice > 0 ? slice : 1, kHookChunk);  // chunks in the current slice
         PhaseTimer pt("br.hook", s);
-        k_hook<<<grid_for(c1 * kHookChunk, kHookChunk), kHookChunk, 0, s>>>(edges, m, 0, c1, spread, n, par,
-                                                                           is_tree, nullptr, st);
-        note_launch();
-        if (c1 < nchunks) {
-            k_compress<<<gn, 256, 0, s>>>(n, par, st);
+        for (int64_t c0 = 0; c0 < nchunks;) {
+            const int64_t c1 = (C.doubling || c0 == 0) ? (c0 + w < nchunks ? c0 + w : nchunks) : nchunks;
+            if (c0 > 0) {
+                k_compress<<<gn, 256, 0, s>>>(n, par, st);
+                note_launch();
+                if (C.giant) {
+                    k_giant<<<1, kGiantSample, 0, s>>>(par, n, giant);
+                    note_launch();
+                }
+            }
+            k_hook<<<grid_for((c1 - c0) * kHookChunk, kHookChunk), kHookChunk, 0, s>>>(
+                edges, m, c0, c1, spread, n, par, is_tree, nullptr, (c0 > 0 && C.giant) ? giant : nullptr, st);
             note_launch();
-            k_hook<<<grid_for((nchunks - c1) * kHookChunk, kHookChunk), kHookChunk, 0, s>>>(
-                edges, m, c1, nchunks, spread, n, par, is_tree, nullptr, st);
-            note_launch();
+            c0 = c1;
+            w *= 2;
         }
     }
     {
@@ -731,7 +772,7 @@ extern "C" etl_status two_edge_cc(const int32_t *edges, int64_t m, int32_t n, in
     note_launch();
     if (m > 0) {  // connected components of the graph without its bridges; labels = smallest vertex
         k_hook<<<grid_for(m, kHookChunk), kHookChunk, 0, s>>>(edges, m, 0, hook_positions(m), false, n, label,
-                                                            nullptr, is_bridge, st);
+                                                            nullptr, is_bridge, nullptr, st);
         note_launch();
         k_compress<<<gn, 256, 0, s>>>(n, label, st);
         note_launch();

@@ -22,8 +22,9 @@ int num_sms();
 
 // Stream-ordered device allocation from the library's own per-device memory
 // pool, which keeps freed memory reserved (release threshold = max) so that
-// repeated calls do not pay for re-mapping; while the stream is being
-// captured into a graph the default pool is used (graph memory nodes).
+// repeated calls do not pay for re-mapping, and never reuses a block freed on
+// another stream by making this stream wait for that one; while the stream is
+// being captured into a graph the default pool is used (graph memory nodes).
 // Freed with cudaFreeAsync. Returns cudaSuccess or the allocator's error.
 cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
 
@@ -152,7 +153,9 @@ struct SortParams {
 SortParams &sort_params();
 
 struct CcParams {
-    int first_slice_quarters = 4;  // edges hooked before the first compression, in units of n/4
+    int first_slice_quarters = 2;  // edges hooked before the first compression, in units of n/4
+    bool doubling = false;         // later slices double in size, each after a compression
+    bool giant = true;             // after a compression, the most frequent root ranks above all
 };
 CcParams &cc_params();
 

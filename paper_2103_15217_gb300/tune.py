@@ -34,7 +34,9 @@ SPACE = [
     ("rank_blocks_per_sm", [4, 8, 16]),
     ("rmq_levels_per_pass", [1, 2, 3]),
     ("rmq_block", [256, 512]),
-    ("cc_first_slice", [2, 8, 16]),
+    ("cc_first_slice", [1, 2, 4, 8]),
+    ("cc_doubling", [0, 1]),
+    ("cc_giant", [0, 1]),
     ("rmq_blocked", [0, 1]),
     ("sort_rounds", [8, 16]),
 ]
