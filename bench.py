@@ -517,20 +517,28 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
         for s_ in side:
             stream.wait_stream(s_)
 
+    host_s = []
+
     def timed(one):
         for _ in range(max(1, args.warmup)):
             one()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
+        host_s.clear()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for i in range(args.steps):
+            h0 = time.perf_counter()
             one()
-        b.record(stream)
+            host_s.append(time.perf_counter() - h0)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / 1e3 / args.steps
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        return evs[0].elapsed_time(evs[-1]) / 1e3 / args.steps, per
 
-    t_seq = max_over_ranks(timed(one_sequential), world, dev)
-    t = max_over_ranks(timed(one_pipelined), world, dev)
+    t_seq, _ = timed(one_sequential)
+    t_seq = max_over_ranks(t_seq, world, dev)
+    t, per_step = timed(one_pipelined)
+    t = max_over_ranks(t, world, dev)
     # copy bandwidth alone, for context: every input of a step in, every result out, nothing else
     dsts = [torch.empty_like(x[k], device=dev) for _, x in jobs for k in ("parent", "u", "v", "edges") if k in x]
     srcs = [x[k] for _, x in jobs for k in ("parent", "u", "v", "edges") if k in x]
@@ -546,6 +554,8 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
     del dsts
     return {"value": units * world / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": t * 1e3, "sequential_ms_per_step": t_seq * 1e3,
+            "step_ms_min_median_max": [min(per_step), statistics.median(per_step), max(per_step)],
+            "host_enqueue_ms_per_step": 1e3 * statistics.median(host_s),
             "h2d_only_ms_per_step": h2d_s * 1e3, "h2d_gb_per_s": h2d / h2d_s / 1e9,
             "timing": "public API calls, eager; each instance on its own stream (copy in, compute, copy out), "
                       "query pairs copied on side streams during preprocessing; host inputs pinned"}

@@ -148,19 +148,34 @@ constexpr int kGiantSample = 1024;
 
 __global__ void __launch_bounds__(kGiantSample) k_giant(const int32_t *__restrict__ par, int32_t n,
                                                          int32_t *__restrict__ giant) {
-    __shared__ int32_t root[kGiantSample];
+    constexpr int kSlots = 2 * kGiantSample;  // open-addressing table of (root, count)
+    __shared__ int32_t key[kSlots], cnt[kSlots];
     __shared__ unsigned long long best;
     const int i = threadIdx.x;
-    const int32_t v = int32_t((uint64_t(i) * 2654435761u + 12345u) % uint64_t(n));
-    root[i] = __ldcg(par + v);
+    for (int j = i; j < kSlots; j += kGiantSample) {
+        key[j] = -1;
+        cnt[j] = 0;
+    }
     if (i == 0) best = 0;
     __syncthreads();
-    int32_t c = 0;
-    for (int j = 0; j < kGiantSample; ++j) c += root[j] == root[i];
-    // largest count, then smallest root id: pack (count, ~root) and take the maximum
-    atomicMax(&best, (static_cast<unsigned long long>(c) << 32) | uint32_t(~uint32_t(root[i])));
+    const int32_t v = int32_t((uint64_t(i) * 2654435761u + 12345u) % uint64_t(n));
+    const int32_t r = __ldcg(par + v);
+    int slot = -1;
+    uint32_t h = (uint32_t(r) * 2654435761u) >> 21;  // 11 bits: kSlots = 2048
+    for (int probe = 0; probe < kSlots; ++probe, h = (h + 1) & (kSlots - 1)) {
+        const int32_t prev = atomicCAS(&key[h], -1, r);
+        if (prev == -1 || prev == r) {
+            slot = int(h);
+            atomicAdd(&cnt[h], 1);
+            break;
+        }
+    }
     __syncthreads();
-    if (i == 0) *giant = int32_t(~uint32_t(best & 0xffffffffu));
+    // largest count, then smallest root id: pack (count, ~root) and take the maximum
+    if (slot >= 0)
+        atomicMax(&best, (static_cast<unsigned long long>(cnt[slot]) << 32) | uint32_t(~uint32_t(r)));
+    __syncthreads();
+    if (i == 0) *giant = best ? int32_t(~uint32_t(best & 0xffffffffu)) : -1;
 }
 
 // forest edges packed in edge order: tuv[2t] = u, tuv[2t+1] = v, tedge[t] = e
