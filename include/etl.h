@@ -290,6 +290,9 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  *                           of a sample (the giant component's) outranks all
  *                           others when roots are hooked, so it never moves;
  *                           0: plain smaller-id order (1)
+ *   ETL_TUNE_SORT_BALLOT    1: the radix scatter finds the lanes holding the
+ *                           same digit with eight warp ballots; 0: with
+ *                           __match_any_sync (1)
  * Unknown keys or out-of-range values return ETL_EINVAL.
  */
 enum {
@@ -303,7 +306,8 @@ enum {
     ETL_TUNE_RMQ_BLOCKED = 8,
     ETL_TUNE_SORT_ROUNDS = 9,
     ETL_TUNE_CC_DOUBLING = 10,
-    ETL_TUNE_CC_GIANT = 11
+    ETL_TUNE_CC_GIANT = 11,
+    ETL_TUNE_SORT_BALLOT = 12
 };
 etl_status etl_tune_set(int32_t key, int32_t value);
 etl_status etl_tune_get(int32_t key, int32_t *value);

@@ -33,7 +33,7 @@ EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_pr
 TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
              "rmq_levels_per_pass": 5, "rmq_block": 6, "cc_first_slice": 7,
              "rmq_blocked": 8, "sort_rounds": 9, "cc_doubling": 10,
-             "cc_giant": 11}
+             "cc_giant": 11, "sort_ballot": 12}
 
 _lock = threading.Lock()
 _lib = None

@@ -142,6 +142,10 @@ extern "C" etl_status etl_tune_set(int32_t key, int32_t value) {
             if (value != 0 && value != 1) return ETL_EINVAL;
             cc_params().giant = value != 0;
             return ETL_OK;
+        case ETL_TUNE_SORT_BALLOT:
+            if (value != 0 && value != 1) return ETL_EINVAL;
+            sort_params().ballot = value != 0;
+            return ETL_OK;
         default:
             return ETL_EINVAL;
     }
@@ -162,6 +166,7 @@ extern "C" etl_status etl_tune_get(int32_t key, int32_t *value) {
         case ETL_TUNE_SORT_ROUNDS: *value = sort_params().rounds; return ETL_OK;
         case ETL_TUNE_CC_DOUBLING: *value = cc_params().doubling ? 1 : 0; return ETL_OK;
         case ETL_TUNE_CC_GIANT: *value = cc_params().giant ? 1 : 0; return ETL_OK;
+        case ETL_TUNE_SORT_BALLOT: *value = sort_params().ballot ? 1 : 0; return ETL_OK;
         default: return ETL_EINVAL;
     }
 }

@@ -148,7 +148,8 @@ struct RankParams {
 RankParams &rank_params();
 
 struct SortParams {
-    int rounds = 8;  // 32-element rounds per warp in the radix passes: tiles of 256 * rounds elements
+    int rounds = 8;       // 32-element rounds per warp in the radix passes: tiles of 256 * rounds elements
+    bool ballot = true;   // rank equal digits in a warp by ballots instead of __match_any_sync
 };
 SortParams &sort_params();
 

@@ -7,9 +7,10 @@
 // each group in ascending value order.
 //
 // One pass = per-tile digit histograms -> exclusive scan over (digit, tile) ->
-// stable scatter. Inside a tile each warp ranks its 32-element rounds with
-// __match_any_sync and per-warp smem counters, so the order of equal digits is
-// preserved without any atomics on global memory.
+// stable scatter. Inside a tile each warp ranks its 32-element rounds (peers
+// with the same digit by __match_any_sync or by eight ballots) with per-warp
+// smem counters, so the order of equal digits is preserved without any atomics
+// on global memory.
 #include "etl_internal.cuh"
 
 namespace etl {
@@ -62,7 +63,22 @@ __global__ void __launch_bounds__(kThreads)
     for (int d = threadIdx.x; d < kRadix; d += kThreads) ghist[int64_t(d) * nblocks + blockIdx.x] = h[d];
 }
 
-template <int R>
+// lanes of the warp whose 8-bit digit equals this lane's, among the valid lanes (an invalid lane
+// matches itself only): __match_any_sync, or eight ballots on the digit's bits
+template <bool BALLOT>
+__device__ __forceinline__ unsigned digit_peers(int d, bool valid, int lane) {
+    if (!BALLOT) return __match_any_sync(kFull, valid ? d : kRadix + lane);
+    unsigned peers = __ballot_sync(kFull, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1;
+        const unsigned m = __ballot_sync(kFull, bit);
+        peers &= bit ? m : ~m;
+    }
+    return valid ? peers : (1u << lane);
+}
+
+template <int R, bool BALLOT>
 __global__ void __launch_bounds__(kThreads)
     k_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, const int2 *__restrict__ kv,
               const int32_t *d_count, int64_t n_cap, int shift, int32_t key_limit, const int32_t *__restrict__ goff,
@@ -99,8 +115,8 @@ __global__ void __launch_bounds__(kThreads)
     for (int r = 0; r < kRounds; ++r) {
         const int32_t k = key[r];
         const bool valid = k >= 0 && k < key_limit;  // also false past the end (k = -1)
-        int d = valid ? ((k >> shift) & (kRadix - 1)) : (kRadix + lane);  // invalid lanes get unique dummies
-        unsigned peers = __match_any_sync(kFull, d);
+        const int d = valid ? ((k >> shift) & (kRadix - 1)) : 0;
+        const unsigned peers = digit_peers<BALLOT>(d, valid, lane);
         int pre = 0;
         if (valid) pre = wcnt[warp][d];
         __syncwarp();
@@ -161,8 +177,12 @@ etl_status radix_sort_impl(const int32_t *keys_in, const int32_t *vals_in, const
         int2 *out_kv = buf[p & 1];
         {
             PhaseTimer pt("sort.scatter", s);
-            k_scatter<R><<<nblocks, kThreads, 0, s>>>(keys_in, vals_in, kvin, cnt, cap, shift, key_limit, goff,
-                                                      nblocks, out_kv);
+            if (sort_params().ballot)
+                k_scatter<R, true><<<nblocks, kThreads, 0, s>>>(keys_in, vals_in, kvin, cnt, cap, shift, key_limit,
+                                                                goff, nblocks, out_kv);
+            else
+                k_scatter<R, false><<<nblocks, kThreads, 0, s>>>(keys_in, vals_in, kvin, cnt, cap, shift, key_limit,
+                                                                 goff, nblocks, out_kv);
             note_launch();
             st = last_launch();
         }

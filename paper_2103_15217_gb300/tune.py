@@ -39,6 +39,7 @@ SPACE = [
     ("cc_giant", [0, 1]),
     ("rmq_blocked", [0, 1]),
     ("sort_rounds", [8, 16]),
+    ("sort_ballot", [0, 1]),
 ]
 
 
