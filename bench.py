@@ -469,17 +469,29 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
     h2d = sum(t["parent"].numel() * 4 + t["u"].numel() * 8 for t in h_trees) + sum(g["edges"].numel() * 4 for g in h_graphs)
     d2h = sum(t["out"].numel() * 4 for t in h_trees) + sum(g["out"].numel() for g in h_graphs)
 
+    # device buffers for the inputs and results, allocated once: every step copies its inputs into
+    # them and its results out of them (a fresh allocation per step would make the caching allocator
+    # call cudaMalloc whenever a block is still held by another stream, a stall of tens of ms)
+    for x in h_trees:
+        x["d"] = {k: torch.empty_like(x[k], device=dev) for k in ("parent", "u", "v", "out")}
+    for x in h_graphs:
+        x["d"] = {k: torch.empty_like(x[k], device=dev) for k in ("edges", "out")}
+
     def tree_job(t):
-        p = t["parent"].to(dev, non_blocking=True)
-        u = t["u"].to(dev, non_blocking=True)
-        v = t["v"].to(dev, non_blocking=True)
-        h = etl.lca_preprocess(p)
-        t["out"].copy_(h.query(u, v), non_blocking=True)
+        d = t["d"]
+        d["parent"].copy_(t["parent"], non_blocking=True)
+        d["u"].copy_(t["u"], non_blocking=True)
+        d["v"].copy_(t["v"], non_blocking=True)
+        h = etl.lca_preprocess(d["parent"])
+        h.query(d["u"], d["v"], out=d["out"])
+        t["out"].copy_(d["out"], non_blocking=True)
         h.free()
 
     def graph_job(g):
-        e = g["edges"].to(dev, non_blocking=True)
-        g["out"].copy_(etl.find_bridges(e, g["n"]), non_blocking=True)
+        d = g["d"]
+        d["edges"].copy_(g["edges"], non_blocking=True)
+        etl.find_bridges(d["edges"], g["n"], out=d["out"])
+        g["out"].copy_(d["out"], non_blocking=True)
 
     jobs = [(tree_job, t) for t in h_trees] + [(graph_job, g) for g in h_graphs]
     side = [torch.cuda.Stream() for _ in jobs]
@@ -498,7 +510,8 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
         for s_, t in zip(side, h_trees):
             s_.wait_stream(stream)
             with torch.cuda.stream(s_):
-                handles.append(etl.lca_preprocess(t["parent"].to(dev, non_blocking=True)))
+                t["d"]["parent"].copy_(t["parent"], non_blocking=True)
+                handles.append(etl.lca_preprocess(t["d"]["parent"]))
         for s_, g in zip(side[len(h_trees):], h_graphs):
             s_.wait_stream(stream)
             with torch.cuda.stream(s_):
@@ -506,15 +519,14 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
         for s_, cs, t, h in zip(side, copy_side, h_trees, handles):
             cs.wait_stream(stream)
             with torch.cuda.stream(cs):
-                u = t["u"].to(dev, non_blocking=True)
-                v = t["v"].to(dev, non_blocking=True)
+                t["d"]["u"].copy_(t["u"], non_blocking=True)
+                t["d"]["v"].copy_(t["v"], non_blocking=True)
             s_.wait_stream(cs)
-            u.record_stream(s_)
-            v.record_stream(s_)
             with torch.cuda.stream(s_):
-                t["out"].copy_(h.query(u, v), non_blocking=True)
+                h.query(t["d"]["u"], t["d"]["v"], out=t["d"]["out"])
+                t["out"].copy_(t["d"]["out"], non_blocking=True)
                 h.free()
-        for s_ in side:
+        for s_ in side + copy_side:
             stream.wait_stream(s_)
 
     host_s = []

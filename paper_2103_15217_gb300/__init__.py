@@ -342,14 +342,20 @@ def find_bridges_batch(edges: torch.Tensor, edge_off: torch.Tensor, node_off: to
 
 
 def find_bridges(edges: torch.Tensor, n: int, status: torch.Tensor | None = None, stream=None,
-                 method: str = "tv") -> torch.Tensor:
+                 method: str = "tv", out: torch.Tensor | None = None) -> torch.Tensor:
     """uint8 mask, 1 for every bridge of the undirected multigraph (m, 2).
-    method: "tv" (Tarjan-Vishkin low/high) or "hybrid" (tour levels + Chaitanya-Kothapalli marking)."""
+    method: "tv" (Tarjan-Vishkin low/high) or "hybrid" (tour levels + Chaitanya-Kothapalli marking).
+    out: optional contiguous uint8 device tensor of m entries to write the mask into."""
     lib = load_library()
     if edges.dim() != 2 or edges.shape[1] != 2:
         raise ValueError("edges must have shape (m, 2)")
     m = edges.shape[0]
-    mask = torch.empty(m, dtype=torch.uint8, device=edges.device)
+    if out is None:
+        mask = torch.empty(m, dtype=torch.uint8, device=edges.device)
+    else:
+        if out.dtype != torch.uint8 or out.numel() != m or not out.is_contiguous() or out.device != edges.device:
+            raise ValueError("out must be a contiguous uint8 tensor of m entries on the edges' device")
+        mask = out
     fn = {"tv": lib.find_bridges, "hybrid": lib.find_bridges_hybrid}[method]
     _check("find_bridges", fn(_dev_i32(edges, "edges"), m, int(n), mask.data_ptr(), _status_ptr(status),
                               _stream(stream)))
