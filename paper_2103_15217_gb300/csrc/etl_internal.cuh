@@ -249,9 +249,12 @@ struct BlockedLayout {
 };
 // a table over n entries answering ranges of up to max_len entries
 BlockedLayout blocked_layout(int64_t n, int64_t max_len);
-// x (first n entries of base) must be filled; builds pad, pm, sm and top
+// x (first n entries of base) must be filled; builds pad, pm, sm and top. pairs (int32 entries only):
+// pm and sm interleaved as (pm[i], sm[i]) pairs in the 2N entries after x (then blocked_query, which
+// reads them as separate arrays, must not be used on the table; x and top are unchanged)
 template <class Op>
-etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L, cudaStream_t s);
+etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L, cudaStream_t s,
+                         bool pairs = false);
 
 template <class Op>
 struct BlockedView {
@@ -300,6 +303,7 @@ struct etl_lca_s {
     int64_t ld = 0;             // row length of the sparse table
     int32_t *table = nullptr;   // levels * ld (full sparse table) or the blocked table's allocation
     bool blocked = false;       // table is a blocked two-level table (layout `bl`)
+    void *nrec = nullptr;       // blocked table: per node (pre, pm[pre], sm[pre + 1], 0), int4[n]
     etl::BlockedLayout bl{};
     int32_t *status = nullptr;  // device status word
     bool has_table = false;     // RMQ sparse table built (lca_query available)

@@ -210,9 +210,30 @@ struct LcaView {
     const int32_t *pre, *order, *table, *hstatus, *off;
     BlockedView<OpMin> bv;  // the blocked table (when built instead of the full one)
     int64_t max_len;        // longest range the table answers
+    const int4 *nrec;       // blocked table: per node (pre, pm[pre], sm[pre], size)
 };
 
+// Per node w with p = pre(w): the per-position entries of the blocked table that a query can need
+// from w's side, pm[p] (w has the larger preorder number) and sm[p] (the smaller one), with p and
+// size(w), so that a query reads two 16-byte records instead of pre[] twice, then pm and sm. The
+// table stores (pm, sm) pairs, so this is one 8-byte gather per node.
+__global__ void k_node_rec(const int32_t *__restrict__ pre, const int32_t *__restrict__ size,
+                           const int2 *__restrict__ pmsm, int32_t n, int4 *__restrict__ nrec) {
+    for (int64_t w = gtid(); w < n; w += gstride()) {
+        const int32_t p = pre[w], sz = size[w];
+        const int2 e = (p >= 0 && p < n) ? __ldg(pmsm + p) : make_int2(INT_MAX, INT_MAX);  // bad tree: flagged
+        nrec[w] = make_int4(p, e.x, e.y, sz);
+    }
+}
+
 constexpr int kQueryIlp = 4;
+
+// min of x[lo..hi], a range inside one block of the blocked table (at most 32 entries, one line)
+__device__ __forceinline__ int32_t inblock_min(const int32_t *__restrict__ x, int32_t lo, int32_t hi) {
+    int32_t m = __ldg(x + lo);
+    for (int32_t j = lo + 1; j <= hi; ++j) m = min(m, __ldg(x + j));
+    return m;
+}
 
 // Each thread answers kQueryIlp queries at once so that their dependent
 // gathers (pre, table, order) overlap in flight. BATCH: ids are local to the
@@ -256,6 +277,32 @@ __global__ void __launch_bounds__(256)
             if (!ok[k] || bad_tree) continue;
             if (a[k] == b[k]) {
                 res[k] = a[k];
+            } else if (BLOCKED) {
+                const int4 ra = __ldg(h.nrec + ofs[k] + a[k]), rb = __ldg(h.nrec + ofs[k] + b[k]);
+                const bool a_first = ra.x < rb.x;
+                const int4 x = a_first ? ra : rb, y = a_first ? rb : ra;  // x earlier in preorder
+                lo[k] = x.x + 1;
+                hi[k] = y.x;
+                need[k] = hi[k] - lo[k] + 1 <= h.max_len;  // cannot fail unless max_n was understated
+                if (!need[k]) {
+                    set_status(status, ETL_EINVAL);
+                } else if (y.x < x.x + x.w) {  // y lies in x's subtree: x is the answer
+                    need[k] = false;
+                    res[k] = a_first ? a[k] : b[k];
+                } else if ((x.x >> kRmqBlockLog2) != (hi[k] >> kRmqBlockLog2)) {
+                    // across blocks: x is no ancestor of y, so Q at pre(x) (x's parent, the LCA or below
+                    // it) cannot lower the minimum and the range may start at pre(x) itself: sm[pre x]
+                    // and pm[pre y] come with the records, whole blocks between from the top table
+                    int32_t m = min(x.z, y.y);
+                    const int32_t bl = (x.x >> kRmqBlockLog2) + 1, bh = (hi[k] >> kRmqBlockLog2) - 1;
+                    if (bl <= bh) {
+                        const int l = 31 - __clz(bh - bl + 1);
+                        const int32_t *row = h.bv.top + int64_t(l) * h.bv.nblk;
+                        m = min(m, min(__ldg(row + bl), __ldg(row + bh - (1 << l) + 1)));
+                    }
+                    lo[k] = m;
+                    hi[k] = -1;  // answered
+                }
             } else {
                 const int32_t pa = __ldg(h.pre + ofs[k] + a[k]), pb = __ldg(h.pre + ofs[k] + b[k]);
                 lo[k] = min(pa, pb) + 1;
@@ -266,9 +313,8 @@ __global__ void __launch_bounds__(256)
         }
 #pragma unroll
         for (int k = 0; k < kQueryIlp; ++k)
-            if (need[k])
-                lo[k] = BLOCKED ? blocked_query<OpMin>(h.bv, lo[k], hi[k])
-                                : sparse_query<false>(h.table, h.ld, lo[k], hi[k]);
+            if (need[k] && hi[k] >= 0)  // in one block (blocked table), or the full table
+                lo[k] = BLOCKED ? inblock_min(h.bv.x, lo[k], hi[k]) : sparse_query<false>(h.table, h.ld, lo[k], hi[k]);
 #pragma unroll
         for (int k = 0; k < kQueryIlp; ++k) {
             const int64_t i = base + k * stride;
@@ -291,7 +337,7 @@ void free_handle(etl_lca_s *h) {
     cudaStream_t s = h->stream;
     for (int32_t *p : {h->pre, h->depth, h->size, h->order, h->table, h->status, h->node_off})
         if (p) cudaFreeAsync(p, s);
-    for (void *p : {h->inrec, h->inpath, h->tour_table, static_cast<void *>(h->tpos)})
+    for (void *p : {h->inrec, h->inpath, h->tour_table, static_cast<void *>(h->tpos), h->nrec})
         if (p) cudaFreeAsync(p, s);
     delete h;
 }
@@ -317,6 +363,8 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
     ok = ok && dev_alloc((void **)&h->order, nb, s) == cudaSuccess;
     if (with_table)
         ok = ok && dev_alloc((void **)&h->table, table_bytes, s) == cudaSuccess;
+    if (with_table && h->blocked)
+        ok = ok && dev_alloc((void **)&h->nrec, size_t(n) * sizeof(int4), s) == cudaSuccess;
     ok = ok && dev_alloc((void **)&h->status, sizeof(int32_t), s) == cudaSuccess;
     if (ok && batch)
         ok = dev_alloc((void **)&h->node_off, size_t(k + 1) * sizeof(int32_t), s) == cudaSuccess;
@@ -393,8 +441,16 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
             st = last_launch();
         }
         if (!st && with_table)
-            st = h->blocked ? blocked_build<OpMin>(h->table, n, h->bl, s)
+            st = h->blocked ? blocked_build<OpMin>(h->table, n, h->bl, s, /*pairs=*/true)
                             : sparse_table_build<false>(h->table, n, h->levels, s);
+        if (!st && with_table && h->blocked) {
+            PhaseTimer pt("lca.node_rec", s);
+            k_node_rec<<<grid_for(n, 256), 256, 0, s>>>(
+                h->pre, h->size, reinterpret_cast<const int2 *>(h->table + h->bl.nblk * kRmqBlock), n,
+                static_cast<int4 *>(h->nrec));
+            note_launch();
+            st = last_launch();
+        }
     }
     if (st) {
         free_handle(h);
@@ -409,7 +465,8 @@ etl_status query_launch(etl_lca_t h, const int32_t *inst, const int32_t *u, cons
     LcaView view{h->n,     h->k,      h->levels, h->ld,
                  h->pre,   h->order,  h->table,  h->status,
                  h->node_off, blocked_view<OpMin>(h->table, h->bl),
-                 h->blocked ? blocked_max_len(h->bl) : (int64_t(1) << h->levels) - 1};
+                 h->blocked ? blocked_max_len(h->bl) : (int64_t(1) << h->levels) - 1,
+                 static_cast<const int4 *>(h->nrec)};
     PhaseTimer pt("lca.query", s);
     const int grid = grid_for(ceil_div(q, kQueryIlp), 256);
     if (h->blocked) {

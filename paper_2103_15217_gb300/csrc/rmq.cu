@@ -16,6 +16,7 @@
 // 129 MB L2 for the sizes used here. Rows are padded to a multiple of four
 // entries with the identity.
 #include <climits>
+#include <type_traits>
 
 #include "etl_internal.cuh"
 
@@ -90,8 +91,9 @@ __device__ __forceinline__ int2 shfl_down(int2 v, int d) {
 }
 
 // one warp per block of 32 entries: prefix and suffix op by shuffles, block result -> top level 0;
-// entries in [n, nblk * 32) are set to the identity first
-template <class Op>
+// entries in [n, nblk * 32) are set to the identity first. PAIRS (int32 entries only): pm and sm are
+// stored interleaved, (pm[i], sm[i]) as one 8-byte pair at position i of the 2N entries after x
+template <class Op, bool PAIRS>
 __global__ void k_block_scan(typename Op::T *__restrict__ x, int64_t n, int64_t nblk, typename Op::T *__restrict__ pm,
                              typename Op::T *__restrict__ sm, typename Op::T *__restrict__ top0) {
     using T = typename Op::T;
@@ -113,8 +115,12 @@ __global__ void k_block_scan(typename Op::T *__restrict__ x, int64_t n, int64_t 
             if (lane >= d) p = Op::f(p, up);
             if (lane + d < kRmqBlock) q = Op::f(q, dn);
         }
-        pm[i] = p;
-        sm[i] = q;
+        if constexpr (PAIRS) {
+            reinterpret_cast<int2 *>(pm)[i] = make_int2(p, q);
+        } else {
+            pm[i] = p;
+            sm[i] = q;
+        }
         if (lane == kRmqBlock - 1) top0[b] = p;
     }
 }
@@ -147,7 +153,7 @@ BlockedLayout blocked_layout(int64_t n, int64_t max_len) {
 }
 
 template <class Op>
-etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L, cudaStream_t s) {
+etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L, cudaStream_t s, bool pairs) {
     using T = typename Op::T;
     const int64_t N = L.nblk * kRmqBlock;
     T *top = base + 3 * N;
@@ -156,7 +162,14 @@ etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L
         PhaseTimer pt("rmq.blocks", s);
         int blocks = int(ceil_div(N, 256));
         if (blocks > grid_cap) blocks = grid_cap;
-        k_block_scan<Op><<<blocks, 256, 0, s>>>(base, n, L.nblk, base + N, base + 2 * N, top);
+        bool launched = false;
+        if constexpr (std::is_same<T, int32_t>::value) {
+            if (pairs) {
+                k_block_scan<Op, true><<<blocks, 256, 0, s>>>(base, n, L.nblk, base + N, base + 2 * N, top);
+                launched = true;
+            }
+        }
+        if (!launched) k_block_scan<Op, false><<<blocks, 256, 0, s>>>(base, n, L.nblk, base + N, base + 2 * N, top);
         note_launch();
     }
     etl_status st = last_launch();
@@ -173,10 +186,10 @@ etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L
     return st;
 }
 
-template etl_status blocked_build<OpMin>(int32_t *, int64_t, const BlockedLayout &, cudaStream_t);
-template etl_status blocked_build<OpMax>(int32_t *, int64_t, const BlockedLayout &, cudaStream_t);
-template etl_status blocked_build<OpMinMax>(int2 *, int64_t, const BlockedLayout &, cudaStream_t);
-template etl_status blocked_build<OpMinKey>(long long *, int64_t, const BlockedLayout &, cudaStream_t);
+template etl_status blocked_build<OpMin>(int32_t *, int64_t, const BlockedLayout &, cudaStream_t, bool);
+template etl_status blocked_build<OpMax>(int32_t *, int64_t, const BlockedLayout &, cudaStream_t, bool);
+template etl_status blocked_build<OpMinMax>(int2 *, int64_t, const BlockedLayout &, cudaStream_t, bool);
+template etl_status blocked_build<OpMinKey>(long long *, int64_t, const BlockedLayout &, cudaStream_t, bool);
 
 RmqParams &rmq_params() {
     static RmqParams p;

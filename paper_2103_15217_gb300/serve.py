@@ -95,7 +95,7 @@ def resident_bytes(sizes, blocked: bool = True) -> int:
     if blocked:
         nblk = (n + 31) // 32
         levels = int(np.ceil(np.log2(max(2, (max(sizes) + 31) // 32 + 1)))) + 1
-        return 16 * n + 4 * (3 * nblk * 32 + nblk * levels)
+        return 32 * n + 4 * (3 * nblk * 32 + nblk * levels)  # + one 16-byte query record per node
     levels = int(np.ceil(np.log2(max(2, max(sizes))))) + 1
     return 16 * n + 4 * ((n + 3) // 4 * 4) * levels
 
