@@ -184,12 +184,25 @@ __global__ void k_node_stats(RankResult rr, const int32_t *__restrict__ succ, in
 // Q in preorder: position i holds pre(parent(order[i])); two gathers and a coalesced write (a
 // scatter to pre(v) would cost a read-for-fill and a write-back per random sector). The root is
 // never inside a query range.
+constexpr int kGatherIlp = 4;  // positions per thread per step whose dependent gathers are in flight together
+
 __global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *__restrict__ pre,
                              const int32_t *__restrict__ order, int32_t n, int32_t *__restrict__ q0) {
-    for (int64_t i = gtid(); i < n; i += gstride()) {
-        const int32_t v = order[i];
-        const int32_t p = (v >= 0 && v < n) ? parent[v] : -1;
-        q0[i] = (p >= 0 && p < n) ? __ldg(pre + p) : -1;
+    const int64_t step = gstride() * kGatherIlp;
+    for (int64_t base = blockIdx.x * int64_t(blockDim.x) * kGatherIlp + threadIdx.x; base < n; base += step) {
+        int32_t v[kGatherIlp], p[kGatherIlp];
+#pragma unroll
+        for (int j = 0; j < kGatherIlp; ++j) {
+            const int64_t i = base + int64_t(j) * blockDim.x;
+            v[j] = i < n ? order[i] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < kGatherIlp; ++j) p[j] = (v[j] >= 0 && v[j] < n) ? __ldg(parent + v[j]) : -1;
+#pragma unroll
+        for (int j = 0; j < kGatherIlp; ++j) {
+            const int64_t i = base + int64_t(j) * blockDim.x;
+            if (i < n) q0[i] = (p[j] >= 0 && p[j] < n) ? __ldg(pre + p[j]) : -1;
+        }
     }
 }
 
@@ -219,10 +232,22 @@ struct LcaView {
 // table stores (pm, sm) pairs, so this is one 8-byte gather per node.
 __global__ void k_node_rec(const int32_t *__restrict__ pre, const int32_t *__restrict__ size,
                            const int2 *__restrict__ pmsm, int32_t n, int4 *__restrict__ nrec) {
-    for (int64_t w = gtid(); w < n; w += gstride()) {
-        const int32_t p = pre[w], sz = size[w];
-        const int2 e = (p >= 0 && p < n) ? __ldg(pmsm + p) : make_int2(INT_MAX, INT_MAX);  // bad tree: flagged
-        nrec[w] = make_int4(p, e.x, e.y, sz);
+    constexpr int kIlp = 4;  // nodes per thread per step, their gathers in flight together
+    const int64_t step = gstride() * kIlp;
+    for (int64_t base = blockIdx.x * int64_t(blockDim.x) * kIlp + threadIdx.x; base < n; base += step) {
+        int32_t p[kIlp];
+        int2 e[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const int64_t w = base + int64_t(j) * blockDim.x;
+            p[j] = w < n ? pre[w] : -1;
+            e[j] = (p[j] >= 0 && p[j] < n) ? __ldg(pmsm + p[j]) : make_int2(INT_MAX, INT_MAX);  // bad tree: flagged
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const int64_t w = base + int64_t(j) * blockDim.x;
+            if (w < n) nrec[w] = make_int4(p[j], e[j].x, e[j].y, size[w]);
+        }
     }
 }
 
