@@ -327,6 +327,9 @@ etl_status etl_profile_get(int32_t i, char *name, int32_t name_len, double *tota
 /* Release the device memory the library keeps reserved in its own stream-ordered memory pools
  * (freed buffers stay reserved for reuse until this call). Synchronous with respect to the pools. */
 etl_status etl_trim(void);
+/* Bytes the library's memory pool of the current device holds reserved (mapped) and in use; 0 and
+ * 0 before its first allocation. ETL_EINVAL for null pointers. */
+etl_status etl_pool_stats(int64_t *reserved, int64_t *used);
 /* Number of kernels this process has launched through the library so far (host-side counter). */
 etl_status etl_launch_count(int64_t *count);
 

@@ -28,7 +28,7 @@ STATUS = {0: "ETL_OK", 1: "ETL_EINVAL", 2: "ETL_ENOMEM", 3: "ETL_ECUDA", 4: "ETL
 EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_preprocess", "lca_query", "lca_status", "lca_arrays",
            "lca_export", "lca_free", "find_bridges", "lca_preprocess_batch", "lca_query_batch", "find_bridges_batch",
            "lca_build_inlabel", "lca_query_inlabel", "lca_query_tour", "lca_naive_preprocess", "lca_naive_query",
-           "lca_preprocess_ex", "etl_trim", "two_edge_cc", "find_bridges_hybrid", "etl_profile_enable", "etl_profile_reset",
+           "lca_preprocess_ex", "etl_trim", "etl_pool_stats", "two_edge_cc", "find_bridges_hybrid", "etl_profile_enable", "etl_profile_reset",
            "etl_profile_count", "etl_profile_get", "etl_launch_count", "etl_tune_set", "etl_tune_get")
 TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
              "rmq_levels_per_pass": 5, "rmq_block": 6, "cc_first_slice": 7,
@@ -80,6 +80,7 @@ def load_library(path: str | None = None):
         lib.two_edge_cc.argtypes = [P, i64, i32, P, P, P]
         lib.find_bridges_hybrid.argtypes = [P, i64, i32, P, P, P]
         lib.etl_trim.argtypes = []
+        lib.etl_pool_stats.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.lca_naive_preprocess.argtypes = [P, i32, P, P, P]
         lib.lca_naive_query.argtypes = [P, i32, P, P, i64, P, P, P]
         lib.lca_query_inlabel.argtypes = [P, P, P, i64, P, P, P]
@@ -292,6 +293,13 @@ def lca_preprocess(parent: torch.Tensor, stream=None, methods: tuple = ("rmq",))
     """Preprocess one tree; methods: any of "rmq" (query), "inlabel" (query_inlabel) and "tour_rmq"
     (query_tour)."""
     return Lca(parent, stream, methods=methods)
+
+
+def pool_stats() -> dict:
+    """Bytes reserved and in use in the library's memory pool on the current device."""
+    r, u = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check("etl_pool_stats", load_library().etl_pool_stats(ctypes.byref(r), ctypes.byref(u)))
+    return {"reserved": r.value, "used": u.value}
 
 
 def trim():

@@ -58,6 +58,22 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
 
 using namespace etl;
 
+extern "C" etl_status etl_pool_stats(int64_t *reserved, int64_t *used) {
+    if (!reserved || !used) return ETL_EINVAL;
+    *reserved = *used = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ETL_ECUDA;
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    if (!g_pool[dev]) return ETL_OK;
+    uint64_t r = 0, u = 0;
+    if (cudaMemPoolGetAttribute(g_pool[dev], cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess ||
+        cudaMemPoolGetAttribute(g_pool[dev], cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess)
+        return ETL_ECUDA;
+    *reserved = int64_t(r);
+    *used = int64_t(u);
+    return ETL_OK;
+}
+
 extern "C" etl_status etl_trim(void) {
     std::lock_guard<std::mutex> g(g_pool_mu);
     for (cudaMemPool_t p : g_pool)
