@@ -443,7 +443,7 @@ def roofline_from_phases(phases, trees, graphs, steps):
 def committed_traffic(phase: str, n_trees: int, n_graphs: int):
     """DRAM bytes per launch of the dominant kernel from the committed ncu capture
     (profiles/k_walk0_traffic.json), or None if that capture is for another kernel,
-    another workload, or an older version of the kernel's source."""
+    another workload, an older version of the kernel's source or other launch parameters."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "k_walk0_traffic.json")) as f:
@@ -454,6 +454,10 @@ def committed_traffic(phase: str, n_trees: int, n_graphs: int):
         return None
     if rec.get("phase") != phase or rec.get("source_sha256") != sha or (n_trees, n_graphs) != (3, 2):
         return None
+    import paper_2103_15217_gb300 as etl
+    tuned = etl.tune_get()
+    if any(tuned.get(k) != v for k, v in rec.get("launch_params", {}).items()):
+        return None  # the capture was taken with other launch parameters
     c = rec["cases"]
     return (3 * c["lca"]["traffic_bytes"] + c["easy"]["traffic_bytes"] + c["hard"]["traffic_bytes"]) / 5
 

@@ -259,12 +259,12 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  * (paper_2103_15217_gb300/tune.py). Process-wide; set them between calls,
  * not while calls are being enqueued from another thread.
  *   ETL_TUNE_RANK_K0_LOG2   level-0 splitter density of the list ranker: one
- *                           splitter per 2^k elements, k in [1, 8] (default 4)
+ *                           splitter per 2^k elements, k in [1, 8] (default 5)
  *   ETL_TUNE_RANK_K_LOG2    density at the upper ranking levels, [1, 8] (4)
  *   ETL_TUNE_RANK_BLOCK     threads per block of the walk kernels, one of
- *                           64, 128, 256, 512, 1024 (256)
+ *                           64, 128, 256, 512, 1024 (128)
  *   ETL_TUNE_RANK_BLOCKS_PER_SM  resident walk blocks per SM, block * value
- *                           <= 2048 (8)
+ *                           <= 2048 (4)
  *   ETL_TUNE_RMQ_LEVELS_PER_PASS sparse-table levels built per streaming
  *                           pass, 1..3 (3)
  *   ETL_TUNE_RMQ_BLOCK      threads per block of the sparse-table build,

@@ -140,10 +140,10 @@ struct RankResult {
 };
 
 struct RankParams {
-    int k0_log2 = 4;     // level-0 splitter density: one in 2^k0_log2 elements
+    int k0_log2 = 5;     // level-0 splitter density: one in 2^k0_log2 elements
     int k_log2 = 4;      // density at the upper levels
-    int block = 256;     // threads per block of the walk kernels
-    int blocks_per_sm = 8;
+    int block = 128;     // threads per block of the walk kernels
+    int blocks_per_sm = 4;  // 512 walkers per SM: more of them measured slower (DRAM contention)
 };
 RankParams &rank_params();
 
