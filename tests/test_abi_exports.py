@@ -56,6 +56,30 @@ def test_host_side_validation(lib):
     assert lib.etl_list_rank(None, 4, 0, None, None, None) == 1
     assert lib.etl_list_rank(ctypes.c_void_p(16), 4, 4, ctypes.c_void_p(16), None, None) == 1
     assert lib.lca_free(None) == 0
+    big = 1 << 30  # one past the largest tree (2^30 - 1 nodes: two list elements per node in 31 bits)
+    assert lib.lca_preprocess(ctypes.c_void_p(16), big, None, ctypes.byref(h)) == 1
+    for flags in (0, 8, 16, -1):  # no method, or an unknown bit
+        assert lib.lca_preprocess_ex(ctypes.c_void_p(16), 5, flags, None, ctypes.byref(h)) == 1
+    assert lib.lca_preprocess_ex(ctypes.c_void_p(16), big, 1, None, ctypes.byref(h)) == 1
+    off = ctypes.c_void_p(32)
+    assert lib.lca_preprocess_batch(ctypes.c_void_p(16), off, 0, 5, 5, None, ctypes.byref(h)) == 1   # k < 1
+    assert lib.lca_preprocess_batch(ctypes.c_void_p(16), off, 2, 5, 6, None, ctypes.byref(h)) == 1   # max_n > n
+    assert lib.lca_preprocess_batch(ctypes.c_void_p(16), off, 6, 5, 1, None, ctypes.byref(h)) == 1   # k > n
+    assert lib.lca_preprocess_batch(ctypes.c_void_p(16), None, 2, 5, 3, None, ctypes.byref(h)) == 1
+    for fn in (lib.lca_query_inlabel, lib.lca_query_tour, lib.lca_query_batch):
+        args = (None,) * (8 if fn is lib.lca_query_batch else 7)
+        assert fn(*args) == 1
+    assert lib.find_bridges_batch(None, None, None, 1, 4, 4, None, None, None) == 1
+    assert lib.two_edge_cc(None, 3, 4, None, None, None) == 1
+    assert lib.etl_pool_stats(None, None) == 1
+    v = ctypes.c_int32(0)
+    assert lib.etl_tune_get(999, ctypes.byref(v)) == 1
+    assert lib.etl_tune_set(999, 1) == 1
+    for key, bad in ((1, 0), (1, 9), (3, 100), (5, 4), (7, 0), (8, 2), (9, 12), (12, 2)):
+        assert lib.etl_tune_set(key, bad) == 1, (key, bad)
+    for key in range(1, 13):  # every key reads back, and writing back its value is accepted
+        assert lib.etl_tune_get(key, ctypes.byref(v)) == 0
+        assert lib.etl_tune_set(key, v.value) == 0
 
 
 def test_product_does_not_import_oracle():
