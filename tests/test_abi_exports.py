@@ -66,9 +66,9 @@ def test_host_side_validation(lib):
     assert lib.lca_preprocess_batch(ctypes.c_void_p(16), off, 2, 5, 6, None, ctypes.byref(h)) == 1   # max_n > n
     assert lib.lca_preprocess_batch(ctypes.c_void_p(16), off, 6, 5, 1, None, ctypes.byref(h)) == 1   # k > n
     assert lib.lca_preprocess_batch(ctypes.c_void_p(16), None, 2, 5, 3, None, ctypes.byref(h)) == 1
-    for fn in (lib.lca_query_inlabel, lib.lca_query_tour, lib.lca_query_batch):
-        args = (None,) * (8 if fn is lib.lca_query_batch else 7)
-        assert fn(*args) == 1
+    assert lib.lca_query_inlabel(None, None, None, 4, None, None, None) == 1   # no handle
+    assert lib.lca_query_tour(None, None, None, 4, None, None, None) == 1
+    assert lib.lca_query_batch(None, None, None, None, 4, None, None, None) == 1
     assert lib.find_bridges_batch(None, None, None, 1, 4, 4, None, None, None) == 1
     assert lib.two_edge_cc(None, 3, 4, None, None, None) == 1
     assert lib.etl_pool_stats(None, None) == 1
