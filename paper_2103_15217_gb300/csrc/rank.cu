@@ -357,12 +357,22 @@ RankParams &rank_params() {
     return p;
 }
 
+// Walks of a list whose successors and records (12 bytes per element) fit in about three quarters of
+// the 129 MB L2 run with every SM full of walkers; on longer lists P.blocks_per_sm blocks per SM: with
+// fewer random sectors in flight fewer are evicted before their reuse (measured on 2^25-element tours:
+// 19% less DRAM traffic, and faster, with 512 walkers per SM than with 2048).
+constexpr int64_t kWalkL2Bytes = int64_t(96) << 20;
+
+int walk_grid(int64_t len, int64_t bytes_per_elem, const RankParams &P) {
+    const int per_sm = len * bytes_per_elem > kWalkL2Bytes ? P.blocks_per_sm : 2048 / P.block;
+    return num_sms() * (per_sm > 0 ? per_sm : 1);
+}
+
 etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, const int32_t *d_head, bool dual,
                      int64_t expect_len, int32_t *status, Workspace &ws, RankResult *out) {
     (void)d_len;  // level 0 always spans the whole array; inert slots carry succ = -1
     cudaStream_t s = ws.stream();
     const RankParams &P = rank_params();
-    const int grid = num_sms() * P.blocks_per_sm;
     cudaFuncSetAttribute(k_pointer_jump, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kPjCap * 4);
 
     // ---- level 0: implicit weights, packed 16-bit local offsets
@@ -379,6 +389,7 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
     etl_status st;
     {
         PhaseTimer pt0("rank.walk0", s);
+        const int grid = walk_grid(len0, 12, P);
         if (dual)
             k_walk0<true><<<grid, P.block, 0, s>>>(succ, len0, d_head, H, packed, rnext, rw1, rw2, ctr, dyn_cap, head1,
                                                     status);
@@ -414,6 +425,7 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
         cudaMemsetAsync(L.loc, 0xff, size_t(L.cap) * sizeof(int4), s);
         {
             PhaseTimer ptw("rank.walk", s);
+            const int grid = walk_grid(L.cap, 28, P);
             k_walk<<<grid, P.block, 0, s>>>(L.succ, L.w1, L.w2, L.base, L.d_add, L.cap, L.d_head, h, L.loc, nn, n1, n2,
                                             c, dcap, hd, status);
         note_launch();
@@ -443,7 +455,7 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
         L.O = ws.get<int32_t>(L.cap);
         if (!ws.ok()) return ETL_ENOMEM;
         int blocks = int(ceil_div(L.cap, 256));
-        if (blocks > grid * 4) blocks = grid * 4;
+        if (blocks > num_sms() * 32) blocks = num_sms() * 32;  // four waves of full occupancy
         PhaseTimer pte("rank.expand", s);
         k_expand<<<blocks, 256, 0, s>>>(L.loc, L.base, L.d_add, L.cap, lv[i + 1].cap, lv[i + 1].R, lv[i + 1].O, L.R,
                                         L.O);
