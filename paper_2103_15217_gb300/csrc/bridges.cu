@@ -21,7 +21,8 @@
 //   u. nlo(x) / nhi(x) = min / max of tin(x) and tin(w) over non-forest
 //   edges (x, w), by atomics (the paper uses a segmented reduction);
 //   placed at tin(x) in tour order, low(u) / high(u) are range-min / -max
-//   queries over [tin(u), tout(u)] (sparse tables, rmq.cu).
+//   queries over [tin(u), tout(u)]: one blocked table of (L, H) pairs by
+//   default, else two full sparse tables (rmq.cu).
 // Phase 4, the test: forest edge {u, parent(u)} is a bridge iff
 //   low(u) >= tin(u) and high(u) <= tout(u), i.e. no non-forest edge leaves
 //   the subtree of u. (Sec. 4.1 states the condition the other way round;

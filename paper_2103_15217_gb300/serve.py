@@ -1,7 +1,7 @@
 """Continuous-batching request server for LCA queries and bridge finding.
 
 Trees are preprocessed once and stay resident on the device (one batched LCA
-handle: Euler tour, preorder, sparse table for all of them). Requests arrive
+handle: Euler tour, preorder, range-minimum table for all of them). Requests arrive
 over time: an LCA request carries a batch of (u, v) pairs for one resident
 tree; a bridge request carries a fresh graph. The server loop
 
@@ -89,8 +89,8 @@ class _Batch:
 
 def resident_bytes(sizes, blocked: bool = True) -> int:
     """Device bytes of a resident batch handle over trees of these sizes: pre, depth, size, order and
-    the range-minimum table (blocked: three int32 arrays of n plus a sparse table over blocks of 32;
-    full: one int32 row of n per level)."""
+    the range-minimum table (blocked: three int32 arrays of n plus a sparse table over blocks of 32,
+    and a 16-byte query record per node; full: one int32 row of n per level)."""
     n = int(sum(sizes))
     if blocked:
         nblk = (n + 31) // 32

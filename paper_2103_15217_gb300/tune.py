@@ -1,16 +1,17 @@
 """Autotuner for the launch parameters of the Euler-tour library.
 
 The knobs change no result, only speed (``etl_tune_set``): the list ranker's
-splitter densities and walk-kernel shape, and the sparse-table build's levels
-per pass and block size. ``autotune`` times candidate settings with CUDA
-events on representative inputs -- a tree preprocessing (tour + ranking +
-sparse table) and a bridge-finding call of the requested size -- and keeps
-the fastest. Results are cached per (GPU name, size bucket) in
+splitter densities and walk-kernel shape, the range tables' form and build
+shape, the radix passes' tile size and ranking, and the connectivity pass's
+hooking schedule. ``autotune`` times candidate settings with CUDA events on
+representative inputs -- a tree preprocessing (tour + ranking + range table)
+and a bridge-finding call of the requested size -- and keeps the fastest. Results are cached per (GPU name, size bucket) in
 ``_build/tune_cache.json`` so later runs start from the tuned values.
 
 The search is coordinate-wise: ranking density first (it sets the length of
-the longest dependent walk), then the walk kernel's shape, then the RMQ
-build; each coordinate keeps the best value found before moving on.
+the longest dependent walk), then the walk kernel's shape, then the other
+knobs in the order of SPACE; each coordinate keeps the best value found before
+moving on.
 """
 
 from __future__ import annotations
