@@ -95,6 +95,34 @@ def _time(fn, reps: int) -> float:
     return statistics.median(ts)
 
 
+def valid(params: dict) -> bool:
+    """Settings the library accepts together (each knob's own range is checked by etl_tune_set)."""
+    return params["rank_block"] * params["rank_blocks_per_sm"] <= 2048
+
+
+def coordinate_search(space, start: dict, measure, is_valid=lambda p: True):
+    """Coordinate-wise search: for each (name, values) of space in turn, try every value with the
+    other knobs at the best setting so far and keep the fastest; measure(params) returns a time
+    (lower is better) or None for a setting to skip. Returns (best, best_time, trials)."""
+    best = dict(start)
+    best_t = measure(best)
+    trials = [(dict(best), best_t)]
+    for name, values in space:
+        for v in values:
+            if v == best[name]:
+                continue
+            cand = dict(best, **{name: v})
+            if not is_valid(cand):
+                continue
+            t = measure(cand)
+            if t is None:
+                continue
+            trials.append((dict(cand), t))
+            if t < best_t:
+                best, best_t = cand, t
+    return best, best_t, trials
+
+
 def autotune(n: int = 1 << 22, reps: int = 3, use_cache: bool = True, verbose: bool = False) -> dict:
     """Tune for trees of about n nodes (and graphs of n/4 nodes, 8 edges per node).
     Applies the best setting and returns {"params": ..., "ms": ..., "trials": ...}."""
@@ -111,28 +139,18 @@ def autotune(n: int = 1 << 22, reps: int = 3, use_cache: bool = True, verbose: b
         h.free()
         find_bridges(edges, gn)
 
-    best = tune_get()
+    def measure(params):
+        try:
+            tune_set(**params)
+        except Exception:
+            return None  # rejected by the library
+        ms = _time(workload, reps)
+        if verbose:
+            print(f"  {params}: {ms:.3f} ms")
+        return ms
+
+    best, best_ms, trials = coordinate_search(SPACE, tune_get(), measure, valid)
     tune_set(**best)
-    best_ms = _time(workload, reps)
-    trials = [(dict(best), best_ms)]
-    for name, values in SPACE:
-        for v in values:
-            if v == best[name]:
-                continue
-            cand = dict(best, **{name: v})
-            if cand["rank_block"] * cand["rank_blocks_per_sm"] > 2048:
-                continue
-            try:
-                tune_set(**cand)
-            except Exception:
-                continue
-            ms = _time(workload, reps)
-            trials.append((dict(cand), ms))
-            if verbose:
-                print(f"  {name}={v}: {ms:.3f} ms (best {best_ms:.3f})")
-            if ms < best_ms:
-                best, best_ms = cand, ms
-        tune_set(**best)
     res = {"params": best, "ms": best_ms, "n": n, "trials": len(trials),
            "default_ms": trials[0][1]}
     cache[key] = res
