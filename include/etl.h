@@ -15,8 +15,11 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *    stream). Every call only enqueues work on that stream and returns; it
  *    never synchronises unless its comment says so. Device memory the call
- *    needs for itself is taken with cudaMallocAsync / cudaFreeAsync on that
- *    same stream.
+ *    needs for itself is taken from the library's own stream-ordered memory
+ *    pool (cudaMallocFromPoolAsync / cudaFreeAsync on that same stream; the
+ *    pool keeps freed memory reserved until etl_trim, and never makes one
+ *    stream wait on another to reuse it); while the stream is being captured
+ *    into a CUDA graph, the default pool's graph allocations are used.
  *  - The return value reports what the host can see at call time: ETL_EINVAL
  *    for bad sizes or null pointers (nothing is enqueued then), ETL_ENOMEM /
  *    ETL_ECUDA for a failed allocation or launch. Errors in the DATA (a parent

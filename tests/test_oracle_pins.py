@@ -192,6 +192,30 @@ def test_random_trees(grasp, seed):
     assert (depth[a] <= np.minimum(depth[u], depth[v])).all()
 
 
+@pytest.mark.parametrize("grasp", [1, 4, None])
+def test_rmq_reading_over_preorder(grasp):
+    # the RMQ form the GPU path uses, checked against brute-force LCAs: with Q[i] = pre(parent(node at
+    # preorder i)), min Q over (pre x, pre y] is pre(LCA) for pre x < pre y; when x is not an ancestor
+    # of y, Q[pre x] >= pre(LCA) too, so the range may start at pre x; when it is, x is the LCA
+    n = 400
+    parent = synth.tree_parent(n, grasp, seed=11)
+    pre, depth, size, _ = oracle.tree_tour(parent)
+    order = np.empty(n, np.int64)
+    order[pre] = np.arange(n)
+    Q = np.array([pre[parent[order[i]]] if parent[order[i]] >= 0 else -1 for i in range(n)])
+    u, v = synth.lca_queries(n, 600, seed=12)
+    for a, b in zip(u.tolist(), v.tolist()):
+        if a == b:
+            continue
+        x, y = (a, b) if pre[a] < pre[b] else (b, a)
+        want = brute.lca(parent, a, b)
+        assert order[Q[pre[x] + 1: pre[y] + 1].min()] == want
+        if pre[y] < pre[x] + size[x]:
+            assert want == x
+        else:
+            assert order[Q[pre[x]: pre[y] + 1].min()] == want
+
+
 def test_path_closed_form():
     n = 5000
     parent = synth.tree_parent(n, 1, seed=4, permute=False)
