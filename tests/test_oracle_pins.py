@@ -170,6 +170,35 @@ def test_all_rooted_trees_bruteforce(n):
     assert count == n ** (n - 1)  # Cayley: n^(n-1) rooted labelled trees
 
 
+def test_all_rooted_trees_n7_lca():
+    # every rooted labelled tree on 7 nodes (7^6 = 117,649) and all 49 query pairs: both LCA oracles
+    # against the definition, the deepest common element of the two ancestor sets (kept as bit masks)
+    n = 7
+    pairs = np.array(list(itertools.product(range(n), repeat=2)), np.int32)
+    u, v = pairs[:, 0].copy(), pairs[:, 1].copy()
+    count = 0
+    for edges in prufer_trees(n):
+        for root in range(n):
+            parent = root_tree(n, edges, root)
+            anc, dep = [0] * n, [0] * n
+            for x in range(n):  # ancestor set (x included) and depth by climbing
+                y, d = x, 0
+                while y != -1:
+                    anc[x] |= 1 << y
+                    y = int(parent[y])
+                    d += 1
+                dep[x] = d
+            want = []
+            for a_, b_ in pairs.tolist():
+                common = anc[a_] & anc[b_]
+                want.append(max((z for z in range(n) if common >> z & 1), key=lambda z: dep[z]))
+            pre, depth, size, tour = oracle.tree_tour(parent)
+            assert oracle.lca_climb(parent, depth, u, v).tolist() == want
+            assert oracle.lca_offline(parent, u, v).tolist() == want
+            count += 1
+    assert count == n ** (n - 1)
+
+
 # --------------------------------------------------------------------------- random trees
 
 
