@@ -245,6 +245,26 @@ def test_rmq_reading_over_preorder(grasp):
             assert order[Q[pre[x]: pre[y] + 1].min()] == want
 
 
+@pytest.mark.parametrize("grasp", [1, 3, 1024, None])
+def test_original_label_climbing(grasp):
+    # before the relabelling every parent has a smaller label than its child, so climbing from the
+    # larger of the two labels until they meet is exact and needs no depths (an independent LCA)
+    n = 20000
+    parent = synth.tree_parent(n, grasp, seed=21, permute=False)
+    u, v = synth.lca_queries(n, 3000, seed=22)
+    want = []
+    for a, b in zip(u.tolist(), v.tolist()):
+        while a != b:
+            if a > b:
+                a = int(parent[a])
+            else:
+                b = int(parent[b])
+        want.append(a)
+    assert oracle.lca_offline(parent, u, v).tolist() == want
+    _, depth, _, _ = oracle.tree_tour(parent)
+    assert oracle.lca_climb(parent, depth, u, v).tolist() == want
+
+
 def test_path_closed_form():
     n = 5000
     parent = synth.tree_parent(n, 1, seed=4, permute=False)
