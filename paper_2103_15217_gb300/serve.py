@@ -100,6 +100,35 @@ def resident_bytes(sizes, blocked: bool = True) -> int:
     return 16 * n + 4 * ((n + 3) // 4 * 4) * levels
 
 
+def form_batch(queue, used: int, budget: int, batching: bool, max_q: int, max_g: int, idle: bool):
+    """Take the next batch from the head of the arrival-ordered queue (a deque, consumed in place):
+    requests join in order while their bytes fit the budget next to `used`, at most max_q LCA queries
+    and max_g graphs per batch (one request when not batching). A request too large for the whole
+    budget runs alone once nothing else is resident (`idle`). Returns (batch, bytes)."""
+    batch, nb, nq, ng = [], 0, 0, 0
+    while queue:
+        r = queue[0]
+        rb = r.bytes()
+        if used + nb + rb > budget:
+            break
+        if batch and not batching:
+            break
+        if r.kind == "lca" and batch and nq + r.units() > max_q:
+            break
+        if r.kind == "bridges" and batch and ng + 1 > max_g:
+            break
+        batch.append(queue.popleft())
+        nb += rb
+        if r.kind == "lca":
+            nq += r.units()
+        else:
+            ng += 1
+    if not batch and idle and queue:
+        r = queue.popleft()  # larger than the whole budget: run it alone
+        batch, nb = [r], r.bytes()
+    return batch, nb
+
+
 class Server:
     def __init__(self, tree_parents, budget_bytes: int = 40 << 30, slots: int = 4,
                  max_batch_queries: int = 1 << 23, max_batch_graphs: int = 16, device=None):
@@ -213,30 +242,10 @@ class Server:
                     del inflight[si]
             free = [i for i in range(len(slots)) if i not in inflight]
             while free and queue:
-                batch, nb, nq, ng = [], 0, 0, 0
-                while queue:
-                    r = queue[0]
-                    rb = r.bytes()
-                    if used + nb + rb > self.budget:
-                        break
-                    if batch and not batching:
-                        break
-                    if r.kind == "lca" and batch and nq + r.u.shape[0] > self.max_q:
-                        break
-                    if r.kind == "bridges" and batch and ng + 1 > self.max_g:
-                        break
-                    batch.append(queue.popleft())
-                    nb += rb
-                    if r.kind == "lca":
-                        nq += r.u.shape[0]
-                    else:
-                        ng += 1
+                batch, nb = form_batch(queue, used, self.budget, batching, self.max_q, self.max_g,
+                                       idle=not inflight and used == self.resident)
                 if not batch:
-                    if not inflight and queue and used == self.resident:
-                        r = queue.popleft()   # larger than the whole budget: run it alone
-                        batch, nb = [r], r.bytes()
-                    else:
-                        break
+                    break
                 si = free.pop(0)
                 b = self._launch(batch, slots[si])
                 b.t_admit = now()
