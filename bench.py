@@ -52,7 +52,10 @@ ALGO = {
     ("rmq.level_min", "tree"): ("node", 8),    # read level l-1, write level l
     ("rmq.level_min", "graph"): ("pos", 8),
     ("rmq.level_max", "graph"): ("pos", 8),
-    ("lca.query", "tree"): ("query", 32),      # u, v 8; pre 8; two table entries 8; order 4; out 4
+    ("lca.query", "tree"): ("query", 32),      # u, v 8; pre of both 8; the two range entries 8; order 4; out 4
+    ("lca.succ", "tree"): ("node", 16),        # child offsets 8, grouped child 4, successor 4 (per node)
+    ("lca.node_rec", "tree"): ("node", 24),    # pre 4, size 4, (pm, sm) 8, record 8 of it used
+    ("rmq.blocks", "tree"): ("node", 12),      # read Q, write pm and sm
     ("sort.scatter", "tree"): ("node", 16),    # read key, value; write key, value
     ("sort.scatter", "graph"): ("arc", 16),
     ("lca.node_stats", "tree"): ("node", 32),  # 2 records 16, write pre/depth/size 12, order 4

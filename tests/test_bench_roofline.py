@@ -1,0 +1,51 @@
+"""The benchmark's roofline entry (host arithmetic, no GPU): the dominant phase
+is picked by device time, its algorithmic bytes per launch come from the
+per-unit table and the workload, and the committed DRAM-traffic record is
+used only for the launch parameters it was taken with."""
+
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def workload():
+    trees = [dict(n=1 << 24, u=np.zeros(1 << 24, np.int32)) for _ in range(3)]
+    graphs = [dict(n=1 << 22, m=(1 << 25) - 1), dict(n=1 << 22, m=(1 << 22) - 1 + (1 << 24))]
+    return trees, graphs
+
+
+def test_dominant_phase_and_algorithmic_bytes():
+    trees, graphs = workload()
+    steps = 4
+    # walk0: 5 launches per step (3 trees + 2 graphs), 1 ms each; query: 3 launches of 0.5 ms
+    phases = {"rank.walk0": (5 * steps * 1.0, 5 * steps), "lca.query": (3 * steps * 0.5, 3 * steps)}
+    r = bench.roofline_from_phases(phases, trees, graphs, steps)
+    assert r["kernel"] == "rank.walk0" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    want = (3 * 2 * (1 << 24) * 12 + 2 * (2 * (1 << 22) - 1) * 12) / 5
+    assert r["bytes_per_launch"] == pytest.approx(want)
+    assert r["avg_launch_ms"] == pytest.approx(1.0)
+    assert r["achieved"] == pytest.approx(want / 1e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["launches_per_step"] == 5
+
+
+def test_traffic_record_needs_its_launch_parameters():
+    import paper_2103_15217_gb300 as etl
+    etl.build()
+    etl.load_library()
+    old = etl.tune_get()
+    try:
+        t = bench.committed_traffic("rank.walk0", 3, 2)
+        assert t is None or t > 0
+        etl.tune_set(rank_k0_log2=3 if old["rank_k0_log2"] != 3 else 4)  # not the capture's setting
+        assert bench.committed_traffic("rank.walk0", 3, 2) is None
+    finally:
+        etl.tune_set(**old)
+    assert bench.committed_traffic("lca.query", 3, 2) is None  # the record is for the walk only
+    assert bench.committed_traffic("rank.walk0", 1, 2) is None  # and for the bench's workload only
