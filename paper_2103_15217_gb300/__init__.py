@@ -47,8 +47,8 @@ class EtlError(RuntimeError):
 
 def build(force: bool = False) -> str:
     """Compile the CUDA library in-tree (nvcc, sm_103a) if its sources changed."""
-    import importlib
-    return importlib.import_module(__name__ + ".build").build(force=force)
+    from . import buildlib  # a submodule named like this function would replace it on import
+    return buildlib.build(force=force)
 
 
 def load_library(path: str | None = None):
