@@ -80,6 +80,9 @@ def parse():
                     help="run one workload of size --n twice (warm-up + one more) and exit; for profilers")
     ap.add_argument("--n", type=int, default=1 << 22)
     ap.add_argument("--grasp", type=int, default=0, help="tree grasp for --case lca (0 = unlimited)")
+    ap.add_argument("--seed", type=int, default=1,
+                    help="seed of the step's synthetic inputs (rank r uses seed + r); the paper's protocol "
+                         "repeats a measurement over five seeds")
     return ap.parse_args()
 
 
@@ -101,9 +104,17 @@ def max_over_ranks(t: float, world: int, device=None) -> float:
     return float(tt.item())
 
 
-def replica_seed(rank: int) -> int:
+def step_stats(ms) -> dict:
+    """Mean, standard deviation, minimum, median and maximum of per-step times (the statistics the
+    paper reports over its repeated runs)."""
+    ms = list(ms)
+    return {"mean": statistics.mean(ms), "std": statistics.pstdev(ms), "min": min(ms),
+            "median": statistics.median(ms), "max": max(ms), "n": len(ms)}
+
+
+def replica_seed(rank: int, base: int = 1) -> int:
     """Each rank runs its own replica of the workload (weak scaling), with its own inputs."""
-    return 1 + rank
+    return base + rank
 
 
 # ------------------------------------------------------------------ inputs
@@ -196,7 +207,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     etl.build()
     etl.load_library()
-    trees, graphs = make_inputs(args.small, seed=replica_seed(rank))
+    trees, graphs = make_inputs(args.small, seed=replica_seed(rank, args.seed))
 
     d_trees = [dict(t, parent_d=torch.from_numpy(t["parent"]).to(dev), u_d=torch.from_numpy(t["u"]).to(dev),
                     v_d=torch.from_numpy(t["v"]).to(dev)) for t in trees]
@@ -319,7 +330,8 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    t_graph = max_over_ranks(statistics.mean(x.elapsed_time(y) / 1e3 for x, y in replay_s), world, dev)
+    replay_ms = [x.elapsed_time(y) for x, y in replay_s]
+    t_graph = max_over_ranks(statistics.mean(replay_ms) / 1e3, world, dev)
     launches = int(round(launches_per_step * args.steps))
     del graph
 
@@ -378,6 +390,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD if not args.small else "small functional check", "units_per_step": units,
                    "timing": "each step is one CUDA-graph replay of the whole path (captured once); "
                              "breakdown and phase timers come from the same number of eager (sequential) steps",
+                   "seed": replica_seed(rank, args.seed),
+                   "step_ms_stats": step_stats(replay_ms),
                    "eager_ms_per_step": t_eager * 1e3,
                    "sequential_graph_ms_per_step": t_seq_graph * 1e3,
                    "concurrency": "the 3 trees and 2 graphs of a step run on 5 parallel graph branches",

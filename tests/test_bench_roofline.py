@@ -49,3 +49,10 @@ def test_traffic_record_needs_its_launch_parameters():
         etl.tune_set(**old)
     assert bench.committed_traffic("lca.query", 3, 2) is None  # the record is for the walk only
     assert bench.committed_traffic("rank.walk0", 1, 2) is None  # and for the bench's workload only
+
+
+def test_step_statistics_and_seeds():
+    s = bench.step_stats([3.0, 1.0, 2.0, 6.0])
+    assert s == {"mean": 3.0, "std": pytest.approx(np.std([3.0, 1.0, 2.0, 6.0])), "min": 1.0, "median": 2.5,
+                 "max": 6.0, "n": 4}
+    assert bench.replica_seed(0) == 1 and bench.replica_seed(3, base=5) == 8
