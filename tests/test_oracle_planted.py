@@ -33,6 +33,16 @@ MUTATIONS = {
         "(uint8_t)(lo < pre[x] || hi >= pre[x] + size[x])"),
     "tv_high_off_by_one": ("hi < pre[x] + size[x])", "hi <= pre[x] + size[x])"),
     "tv_drop_high": ("(uint8_t)(lo >= pre[x] && hi < pre[x] + size[x])", "(uint8_t)(lo >= pre[x])"),
+    "depth_not_incremented": ("depth[c] = depth[v] + 1;", "depth[c] = depth[v];"),
+    "dcel_sort_by_target_first": ("if (ax != bx) return ax < bx ? -1 : 1;\n    if (ay != by) return ay < by ? -1 : 1;",
+                                  "if (ay != by) return ay < by ? -1 : 1;\n    if (ax != bx) return ax < bx ? -1 : 1;"),
+    "dcel_wrap_to_following_entry": (": B[first[x]];", ": B[(i + 1) % na];"),
+    "tv_non_tree_edge_one_end_only": ("        if (pre[a] < nlo[b]) nlo[b] = pre[a];\n        if (pre[a] > nhi[b]) nhi[b] = pre[a];\n",
+                                      ""),
+    "tv_no_subtree_aggregation": ("            if (nlo[x] < nlo[p]) nlo[p] = nlo[x];\n            if (nhi[x] > nhi[p]) nhi[p] = nhi[x];\n",
+                                  "            (void)p;\n"),
+    "two_edge_cc_keeps_bridges": ("        if (br[e]) continue;\n", ""),
+    "two_edge_cc_largest_label": ("if (a < b) uf[b] = a; else uf[a] = b;", "if (a < b) uf[a] = b; else uf[b] = a;"),
 }
 
 PINS = [
@@ -44,6 +54,8 @@ PINS = [
     pins.test_path_closed_form,
     pins.test_bridges_bruteforce_random_multigraphs,
     lambda: pins.test_hard_graph_closed_form(1),
+    pins.test_two_edge_cc_closed_forms,
+    pins.test_two_edge_cc_bruteforce,
 ]
 
 
