@@ -65,3 +65,28 @@ def test_oversize_request_runs_alone_when_idle():
     batch, nb = form_batch(q, used=0, budget=budget, batching=True, max_q=10 ** 9, max_g=16, idle=True)
     assert batch == [big] and nb == big.bytes()
     assert [r.rid for r in q] == [1]
+
+
+def test_summary_percentiles_and_throughput():
+    from paper_2103_15217_gb300.serve import Result, summarize
+    res = [Result(i, "lca", np.zeros(10, np.int32), t_arrive=0.01 * i, t_admit=0.01 * i,
+                  t_done=0.01 * i + 0.001 * (i + 1)) for i in range(100)]
+    s = summarize(res)
+    assert s["requests"] == 100 and s["units"] == 1000
+    assert abs(s["seconds"] - (0.99 + 0.1)) < 1e-12 and abs(s["throughput"] - 1000 / 1.09) < 1e-6
+    assert abs(s["p50_ms"] - 50.5) < 1e-9 and abs(s["p99_ms"] - 99.01) < 1e-9  # latencies 1..100 ms
+    assert abs(s["mean_ms"] - 50.5) < 1e-9
+    assert summarize(res, wall_units=7)["units"] == 7
+
+
+def test_resident_table_forms():
+    from paper_2103_15217_gb300.serve import resident_bytes
+    sizes = [1 << 20, 1 << 16, 1 << 10]
+    n = sum(sizes)
+    blocked, full = resident_bytes(sizes, True), resident_bytes(sizes, False)
+    # both hold at least pre, depth, size and order; the blocked form also a 16-byte record per node
+    assert blocked >= 32 * n and full >= 16 * n
+    # the full sparse table grows with log n per node, the blocked one does not
+    assert full > blocked
+    assert resident_bytes([1 << 22], False) / (1 << 22) > resident_bytes([1 << 12], False) / (1 << 12)
+    assert abs(resident_bytes([1 << 22], True) / (1 << 22) - resident_bytes([1 << 12], True) / (1 << 12)) < 2
