@@ -252,7 +252,8 @@ etl_status lca_free(etl_lca_t h);
  * non-forest edge leaves the subtree of u. Endpoints out of range give
  * ETL_EBADGRAPH in *status (device int32, may be NULL; the call first sets it
  * to 0) and an all-zero mask.
- * n in [1, 2^30], m in [0, 2^31 - 2].
+ * n in [1, 2^30 - 1] (the forest tour of 2(n - 1) half-edges plus a head stays within
+ * the list ranker's 2^31 - 2 elements), m in [0, 2^31 - 2].
  */
 etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
                         void *stream);
@@ -345,7 +346,8 @@ etl_status etl_launch_count(int64_t *count);
  * with at least one node (else ETL_EINVAL in the status word). Writes
  * is_bridge[e] for every edge of every graph, the same as find_bridges on
  * that graph alone. The disjoint union is processed as one graph: bridges of
- * a disjoint union are the bridges of its parts.
+ * a disjoint union are the bridges of its parts. total_n in [k, 2^30 - 1],
+ * total_m in [0, 2^31 - 2].
  */
 etl_status find_bridges_batch(const int32_t *edges, const int32_t *edge_off, const int32_t *node_off, int32_t k,
                               int64_t total_m, int32_t total_n, uint8_t *is_bridge, int32_t *status, void *stream);

@@ -731,7 +731,7 @@ using namespace etl;
 
 extern "C" etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
                                    void *stream) {
-    if (n < 1 || n > (1 << 30) || m < 0 || m > int64_t(INT32_MAX) - 1) return ETL_EINVAL;
+    if (n < 1 || n > (1 << 30) - 1 || m < 0 || m > int64_t(INT32_MAX) - 1) return ETL_EINVAL;
     if (m == 0) return ETL_OK;
     if (!edges || !is_bridge) return ETL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -745,7 +745,7 @@ extern "C" etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, u
 extern "C" etl_status find_bridges_batch(const int32_t *edges, const int32_t *edge_off, const int32_t *node_off,
                                          int32_t k, int64_t total_m, int32_t total_n, uint8_t *is_bridge,
                                          int32_t *status, void *stream) {
-    if (k < 1 || total_n < k || total_n > (1 << 30) || total_m < 0 || total_m > int64_t(INT32_MAX) - 1)
+    if (k < 1 || total_n < k || total_n > (1 << 30) - 1 || total_m < 0 || total_m > int64_t(INT32_MAX) - 1)
         return ETL_EINVAL;
     if (!edge_off || !node_off) return ETL_EINVAL;
     if (total_m == 0) return ETL_OK;
@@ -772,7 +772,7 @@ extern "C" etl_status find_bridges_batch(const int32_t *edges, const int32_t *ed
 
 extern "C" etl_status two_edge_cc(const int32_t *edges, int64_t m, int32_t n, int32_t *label, int32_t *status,
                                   void *stream) {
-    if (n < 1 || n > (1 << 30) || m < 0 || m > int64_t(INT32_MAX) - 1 || !label) return ETL_EINVAL;
+    if (n < 1 || n > (1 << 30) - 1 || m < 0 || m > int64_t(INT32_MAX) - 1 || !label) return ETL_EINVAL;
     if (m > 0 && !edges) return ETL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Workspace ws(s);
@@ -800,7 +800,7 @@ extern "C" etl_status two_edge_cc(const int32_t *edges, int64_t m, int32_t n, in
 
 extern "C" etl_status find_bridges_hybrid(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge,
                                           int32_t *status, void *stream) {
-    if (n < 1 || n > (1 << 30) || m < 0 || m > int64_t(INT32_MAX) - 1) return ETL_EINVAL;
+    if (n < 1 || n > (1 << 30) - 1 || m < 0 || m > int64_t(INT32_MAX) - 1) return ETL_EINVAL;
     if (m == 0) return ETL_OK;
     if (!edges || !is_bridge) return ETL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

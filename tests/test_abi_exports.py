@@ -61,6 +61,11 @@ def test_host_side_validation(lib):
     for flags in (0, 8, 16, -1):  # no method, or an unknown bit
         assert lib.lca_preprocess_ex(ctypes.c_void_p(16), 5, flags, None, ctypes.byref(h)) == 1
     assert lib.lca_preprocess_ex(ctypes.c_void_p(16), big, 1, None, ctypes.byref(h)) == 1
+    fake = ctypes.c_void_p(16)  # never dereferenced: each call below is refused on the host
+    assert lib.find_bridges(fake, 3, big, fake, None, None) == 1           # forest tour past 2^31 - 2
+    assert lib.find_bridges_hybrid(fake, 3, big, fake, None, None) == 1
+    assert lib.two_edge_cc(fake, 3, big, fake, None, None) == 1
+    assert lib.find_bridges_batch(fake, fake, fake, 1, 3, big, fake, None, None) == 1
     off = ctypes.c_void_p(32)
     assert lib.lca_preprocess_batch(ctypes.c_void_p(16), off, 0, 5, 5, None, ctypes.byref(h)) == 1   # k < 1
     assert lib.lca_preprocess_batch(ctypes.c_void_p(16), off, 2, 5, 6, None, ctypes.byref(h)) == 1   # max_n > n
