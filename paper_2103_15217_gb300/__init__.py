@@ -145,6 +145,7 @@ class Lca:
                  max_n: int | None = None, methods: tuple = ("rmq",)):
         lib = load_library()
         self._lib = lib
+        _dev_i32(parent, "parent")  # refuse host tensors before touching any stream
         self.n = parent.numel()
         self.batched = node_off is not None
         self._h = ctypes.c_void_p()
