@@ -406,6 +406,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roofline,
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in sorted(phases.items())},
+        "phase_rooflines": phase_rooflines(phases, trees, graphs, args.steps),
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -415,46 +416,65 @@ def run_ours(args):
     return result if rank == 0 else None
 
 
-def roofline_from_phases(phases, trees, graphs, steps):
-    peaks = {}
+def _peak_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
+            peak = json.load(f).get("hbm_gbs")
     except Exception:
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
+        peak = None
+    return (peak, "measured") if peak else (6800.0, "fallback")
+
+
+def algorithmic_bytes_per_launch(name, trees, graphs):
+    """Algorithmic bytes one launch of phase `name` moves on this workload (the per-unit figure of
+    ALGO times the units of one instance), or None if the phase has no per-unit figure. A phase
+    that both parts run is averaged over one launch per instance."""
+    n_tree, n_graph = len(trees), len(graphs)
+    tree_units = {"node": sum(t["n"] for t in trees) / max(n_tree, 1),
+                  "arc": sum(2 * t["n"] for t in trees) / max(n_tree, 1),
+                  "query": sum(t["u"].shape[0] for t in trees) / max(n_tree, 1)}
+    graph_units = {"edge": sum(g["m"] for g in graphs) / max(n_graph, 1),
+                   "arc": sum(2 * g["n"] - 1 for g in graphs) / max(n_graph, 1),
+                   "pos": sum(2 * g["n"] - 1 for g in graphs) / max(n_graph, 1)}
+    kt, kg = ALGO.get((name, "tree")), ALGO.get((name, "graph"))
+    if kt and kg:
+        return (n_tree * tree_units[kt[0]] * kt[1] + n_graph * graph_units[kg[0]] * kg[1]) / (n_tree + n_graph)
+    if kt:
+        return tree_units[kt[0]] * kt[1]
+    if kg:
+        return graph_units[kg[0]] * kg[1]
+    return None
+
+
+def phase_rooflines(phases, trees, graphs, steps):
+    """Every timed phase with a per-unit byte figure: its algorithmic bytes per launch, average
+    launch time and the bandwidth that makes, against the measured copy peak."""
+    peak, _ = _peak_hbm()
+    out = {}
+    for name, (ms, launches) in sorted(phases.items()):
+        b = algorithmic_bytes_per_launch(name, trees, graphs)
+        if b is None or not launches or ms <= 0:
+            continue
+        avg_s = ms / 1e3 / launches
+        out[name] = {"ms_per_step": ms / steps, "launches_per_step": launches / steps, "bytes_per_launch": b,
+                     "avg_launch_ms": avg_s * 1e3, "achieved_gbs": b / avg_s / 1e9, "frac": b / avg_s / 1e9 / peak}
+    return out
+
+
+def roofline_from_phases(phases, trees, graphs, steps):
+    peak, peak_src = _peak_hbm()
     # dominant phase by total device time
     name, (ms, launches) = max(phases.items(), key=lambda kv: kv[1][0])
-    # units per launch: phases shared by the tree and the graph parts are split by launch count
-    n_tree = len(trees)
-    per_step = launches / steps
-    tree_units = {"node": sum(t["n"] for t in trees) / n_tree, "arc": sum(2 * t["n"] for t in trees) / n_tree,
-                  "query": sum(t["u"].shape[0] for t in trees) / n_tree}
-    graph_units = {"edge": sum(g["m"] for g in graphs) / len(graphs),
-                   "arc": sum(2 * g["n"] - 1 for g in graphs) / len(graphs),
-                   "pos": sum(2 * g["n"] - 1 for g in graphs) / len(graphs)}
-    part = "tree" if (name, "tree") in ALGO else "graph"
-    key = (name, part)
-    if key not in ALGO:
+    bytes_per_launch = algorithmic_bytes_per_launch(name, trees, graphs)
+    if bytes_per_launch is None:
         return {"bound": "hbm", "kernel": name, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
                 "traffic": None, "note": "no algorithmic byte count for this phase"}
-    unit, bpu = ALGO[key]
-    if (name, "graph") in ALGO and (name, "tree") in ALGO:
-        units = (n_tree * tree_units[ALGO[(name, "tree")][0]] * ALGO[(name, "tree")][1] +
-                 len(graphs) * graph_units[ALGO[(name, "graph")][0]] * ALGO[(name, "graph")][1]) / (n_tree + len(graphs))
-        bytes_per_launch = units
-    else:
-        bytes_per_launch = (tree_units if part == "tree" else graph_units)[unit] * bpu
-    if name.startswith("rmq.level"):  # one launch per level; bytes above are per level
-        pass
     avg_s = ms / 1e3 / launches
     achieved = bytes_per_launch / avg_s / 1e9
     traffic = committed_traffic(name, len(trees), len(graphs))
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}
+            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1e3, "launches_per_step": launches / steps}
 
 
 def committed_traffic(phase: str, n_trees: int, n_graphs: int):

@@ -56,3 +56,19 @@ def test_step_statistics_and_seeds():
     assert s == {"mean": 3.0, "std": pytest.approx(np.std([3.0, 1.0, 2.0, 6.0])), "min": 1.0, "median": 2.5,
                  "max": 6.0, "n": 4}
     assert bench.replica_seed(0) == 1 and bench.replica_seed(3, base=5) == 8
+
+
+def test_every_phase_with_a_byte_figure_gets_a_roofline_row():
+    trees, graphs = workload()
+    steps = 2
+    phases = {"rank.walk0": (10.0, 10), "lca.query": (3.0, 6), "rmq.top": (1.0, 30), "br.hook": (4.0, 8)}
+    rows = bench.phase_rooflines(phases, trees, graphs, steps)
+    assert set(rows) == {"rank.walk0", "lca.query", "br.hook"}  # rmq.top has no per-unit figure
+    q = rows["lca.query"]
+    assert q["bytes_per_launch"] == (1 << 24) * 32 and q["avg_launch_ms"] == 0.5 and q["launches_per_step"] == 3
+    assert abs(q["achieved_gbs"] - (1 << 24) * 32 / 0.5e-3 / 1e9) < 1e-9
+    hook = rows["br.hook"]  # graph-only phase: the mean edge count of the two graphs
+    assert hook["bytes_per_launch"] == ((1 << 25) - 1 + (1 << 22) - 1 + (1 << 24)) / 2 * 17
+    # the dominant-kernel entry is the same arithmetic as its row
+    top = bench.roofline_from_phases(phases, trees, graphs, steps)
+    assert top["kernel"] == "rank.walk0" and abs(top["achieved"] - rows["rank.walk0"]["achieved_gbs"]) < 1e-9
