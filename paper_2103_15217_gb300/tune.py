@@ -21,7 +21,6 @@ import math
 import os
 import statistics
 
-import numpy as np
 import torch
 
 from . import find_bridges, lca_preprocess, load_library, tune_get, tune_set

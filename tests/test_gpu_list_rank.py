@@ -3,7 +3,6 @@ definition: a list built from a permutation has rank[perm[i]] = i."""
 
 import numpy as np
 import pytest
-import torch
 
 from _gpu_util import dev, host
 
