@@ -1072,11 +1072,29 @@ def run_oracle_once(sample):
     return units, dt
 
 
+def host_cpu() -> str:
+    """The host CPU as the kernel reports it (model name on x86, implementer / part on Arm)."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if fields.get("model name"):
+        return fields["model name"]
+    if fields.get("CPU part"):
+        return f"{platform.machine()} implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return platform.machine()
+
+
 def cpu_baseline(small: bool):
     sample = oracle_sample(small)
     units, dt = run_oracle_once(sample)
     return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample[-1],
-            "seconds": dt, "host_cores_available": os.cpu_count()}
+            "seconds": dt, "host_cores_available": os.cpu_count(), "host_cpu": host_cpu()}
 
 
 def run_reference(args):
@@ -1096,7 +1114,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "sample": sample[-1]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample[-1]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample[-1],
+                             "host_cores_available": os.cpu_count(), "host_cpu": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

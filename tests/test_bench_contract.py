@@ -28,6 +28,7 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
     assert d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["host_cpu"] and d["cpu_baseline"]["host_cores_available"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"] and "sample" in d["config"]
