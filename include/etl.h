@@ -87,7 +87,10 @@ etl_status etl_list_rank(const int32_t *succ, int64_t len, int32_t head, int32_t
  *    serialise them;
  *  - the first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current) and caches it, so make
- *    that first call before any stream capture on the device.
+ *    that first call before any stream capture on the device. The cache also
+ *    holds the id of the CUDA context the address belongs to: after a
+ *    cudaDeviceReset the next call looks the address up again (make it, too,
+ *    outside any stream capture).
  */
 etl_status etl_list_rank_static(const int32_t *succ, int64_t len, int32_t head, int32_t *rank, int32_t *status,
                                 void *stream);

@@ -513,8 +513,11 @@ etl_status final_rank(const RankResult &r, int64_t len, int32_t *rank, cudaStrea
 //    threads) race on the same scratch and give wrong ranks: serialise them.
 //  * The host cannot use the array's name as a device address, so the first
 //    call on each device looks the address up with cudaGetSymbolAddress (with
-//    that device current) and caches it; that first call should therefore
-//    come before any stream capture on that device.
+//    that device current) and caches it with the id of the CUDA context it
+//    belongs to; that first call should therefore come before any stream
+//    capture on that device. When the context changes (cudaDeviceReset, or
+//    the primary context destroyed and made again), the next call sees the
+//    new context id and repeats the look-up instead of using a stale address.
 namespace etl {
 namespace {
 
@@ -539,19 +542,53 @@ struct StaticArena {
 
 std::mutex g_static_mu;
 void *g_static_addr[64] = {nullptr};
+unsigned long long g_static_ctx[64] = {0};
 
-// once per device, with that device current: the device address of the scratch array
+// The driver's cuCtxGetCurrent / cuCtxGetId, reached through the runtime (no link against libcuda).
+using CtxGetCurrentFn = int (*)(void **);
+using CtxGetIdFn = int (*)(void *, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+std::once_flag g_ctx_fns_once;
+
+// id of the calling thread's current CUDA context (unique over the process's lifetime); false when
+// there is no current context or the driver entry points are unavailable
+bool current_context_id(unsigned long long *id) {
+    std::call_once(g_ctx_fns_once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!g_ctx_get_current || !g_ctx_get_id) return false;
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return false;
+    return g_ctx_get_id(ctx, id) == 0;
+}
+
+// with the device current: the device address of the scratch array, looked up once per device and
+// context (and again after the context changed)
 etl_status static_scratch(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ETL_ECUDA;
     std::lock_guard<std::mutex> g(g_static_mu);
-    if (!g_static_addr[dev]) {
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    if (!g_static_addr[dev] || !have_id || g_static_ctx[dev] != id) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_rank_scratch) != cudaSuccess || !p) return ETL_ECUDA;
         if (cudaFuncSetAttribute(k_pointer_jump, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kPjCap * 4) !=
             cudaSuccess)
             return ETL_ECUDA;
+        // the look-up made the device's primary context current if it was not yet
+        if (!current_context_id(&id)) return ETL_ECUDA;
         g_static_addr[dev] = p;
+        g_static_ctx[dev] = id;
     }
     *out = g_static_addr[dev];
     return ETL_OK;
