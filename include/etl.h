@@ -19,7 +19,9 @@
  *    pool (cudaMallocFromPoolAsync / cudaFreeAsync on that same stream; the
  *    pool keeps freed memory reserved until etl_trim, and never makes one
  *    stream wait on another to reuse it); while the stream is being captured
- *    into a CUDA graph, the default pool's graph allocations are used.
+ *    into a CUDA graph, the default pool's graph allocations are used. The
+ *    _ws variants (end of this header) take that memory from a caller-owned
+ *    buffer instead and allocate nothing.
  *  - The return value reports what the host can see at call time: ETL_EINVAL
  *    for bad sizes or null pointers (nothing is enqueued then), ETL_ENOMEM /
  *    ETL_ECUDA for a failed allocation or launch. Errors in the DATA (a parent
@@ -339,6 +341,17 @@ etl_status etl_trim(void);
 etl_status etl_pool_stats(int64_t *reserved, int64_t *used);
 /* Number of kernels this process has launched through the library so far (host-side counter). */
 etl_status etl_launch_count(int64_t *count);
+/*
+ * Measurement aid (not part of the method): the memory access pattern of one
+ * step of the list-ranking walk of Sec. 2.2 -- read succ[j] at a random index
+ * j, write an 8-byte record out[j] = (succ[j], i) at the same index -- for
+ * j = order[i], i in [0, n), with every gather independent (no chain of
+ * dependent loads). order is a DEVICE int32[n] permutation of [0, n) (entries
+ * outside it are skipped), succ DEVICE int32[n], out DEVICE 8-byte records[n].
+ * Its rate is the ceiling of a walk over a list in random order, against which
+ * the benchmark reports the walk. n in [1, 2^31 - 1].
+ */
+etl_status etl_probe_gather_scatter(const int32_t *order, const int32_t *succ, int64_t n, void *out, void *stream);
 
 /*
  * find_bridges_batch: k independent graphs in one launch sequence.
@@ -376,6 +389,80 @@ etl_status find_bridges_hybrid(const int32_t *edges, int64_t m, int32_t n, uint8
  * *status (device, may be NULL; zeroed first) holds the code.
  */
 etl_status two_edge_cc(const int32_t *edges, int64_t m, int32_t n, int32_t *label, int32_t *status, void *stream);
+
+/* ------------------------------------------------------------------ caller-owned workspaces
+ * The problem statements of Sec. 3 (LCA: preprocess a tree, then answer
+ * queries) and Sec. 4.1 (bridges of a graph) need scratch memory on the way:
+ * the tour's successor array, the ranking's sublist records, sort buffers and
+ * so on. The plain entry points take it from the library's memory pool. The
+ * _ws variants below take ALL of it from one device buffer the caller owns
+ * and allocate nothing, so a caller with a fixed memory plan, or one that
+ * captures the calls into a CUDA graph and wants no graph memory nodes, can
+ * size and place every byte itself.
+ *
+ * etl_workspace_size: *bytes = the size of the buffer a _ws call of this kind
+ * and these sizes needs, for the tuning parameters in force (query it again
+ * after etl_tune_set). It is exact: the library runs the same entry point once
+ * with a counting arena on a private stream whose work is captured into a CUDA
+ * graph and discarded unlaunched (nothing runs on the device and nothing is
+ * allocated on it). Call it outside any stream capture on this thread.
+ *   kind                      n            m_or_q
+ *   ETL_WS_LIST_RANK          len          (unused)
+ *   ETL_WS_LCA_PREPROCESS     n            (unused)   includes the handle's tables
+ *   ETL_WS_LCA_QUERY          n            q          always 0: lca_query,
+ *                                                     lca_query_batch need no scratch
+ *   ETL_WS_FIND_BRIDGES       n            m
+ * etl_workspace_size_batch: the same for lca_preprocess_batch_ws
+ * (ETL_WS_LCA_PREPROCESS: third argument = max_n) and find_bridges_batch_ws
+ * (ETL_WS_FIND_BRIDGES: third argument = total_m), k instances, total_n nodes.
+ * Sizes outside an entry point's limits, or an unknown kind: ETL_EINVAL.
+ */
+enum { ETL_WS_LIST_RANK = 1, ETL_WS_LCA_PREPROCESS = 2, ETL_WS_LCA_QUERY = 3, ETL_WS_FIND_BRIDGES = 4 };
+etl_status etl_workspace_size(int32_t kind, int64_t n, int64_t m_or_q, size_t *bytes);
+etl_status etl_workspace_size_batch(int32_t kind, int32_t k, int64_t total_n, int64_t max_n_or_total_m,
+                                    size_t *bytes);
+
+/*
+ * The _ws variants: the same arguments, results and error rules as the entry
+ * point without the suffix, plus ws (DEVICE memory owned by the caller, any
+ * alignment) and ws_bytes. They call no allocator (cudaMalloc*, memory pools,
+ * graph memory nodes): every byte the call needs comes from ws, so they can be
+ * captured into a CUDA graph without adding memory nodes to it.
+ *  - ws_bytes >= etl_workspace_size(...) for the same sizes; a smaller buffer
+ *    returns ETL_ENOMEM, possibly after part of the work was enqueued into ws
+ *    (the outputs are then unspecified). ws == NULL: ETL_EINVAL.
+ *  - ws belongs to the call until its work on `stream` has finished; the
+ *    caller may then reuse it -- except for lca_preprocess_ws /
+ *    lca_preprocess_batch_ws, whose handle keeps its tables inside ws: keep ws
+ *    alive and unmodified until lca_free(h) (which then frees only the host
+ *    side of the handle). Such a handle takes no further structures
+ *    (lca_build_inlabel returns ETL_EINVAL).
+ *  - Two calls that use the same ws at the same time on the GPU race.
+ */
+etl_status etl_list_rank_ws(const int32_t *succ, int64_t len, int32_t head, int32_t *rank, int32_t *status,
+                            void *ws, size_t ws_bytes, void *stream);
+etl_status lca_preprocess_ws(const int32_t *parent, int32_t n, void *ws, size_t ws_bytes, void *stream,
+                             etl_lca_t *out);
+etl_status lca_preprocess_batch_ws(const int32_t *parent, const int32_t *node_off, int32_t k, int32_t total_n,
+                                   int32_t max_n, void *ws, size_t ws_bytes, void *stream, etl_lca_t *out);
+etl_status find_bridges_ws(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_bridge, int32_t *status,
+                           void *ws, size_t ws_bytes, void *stream);
+etl_status find_bridges_batch_ws(const int32_t *edges, const int32_t *edge_off, const int32_t *node_off, int32_t k,
+                                 int64_t total_m, int32_t total_n, uint8_t *is_bridge, int32_t *status, void *ws,
+                                 size_t ws_bytes, void *stream);
+
+/*
+ * etl_status_get: waits for `stream`, then copies the device status word
+ * *d_status (the data-error word a call on that stream wrote: 0 or an
+ * etl_status code) to the HOST int32 *h_status. Synchronising; not for use
+ * while `stream` is being captured.
+ */
+etl_status etl_status_get(void *stream, const int32_t *d_status, int32_t *h_status);
+
+/* Number of device allocations the library has requested so far in this
+ * process (pool or graph allocations; carving from a caller's workspace does
+ * not count). Host-side counter. */
+etl_status etl_alloc_count(int64_t *count);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,11 @@ EXPORTS = ("etl_status_string", "etl_list_rank", "etl_list_rank_static", "lca_pr
            "lca_export", "lca_free", "find_bridges", "lca_preprocess_batch", "lca_query_batch", "find_bridges_batch",
            "lca_build_inlabel", "lca_query_inlabel", "lca_query_tour", "lca_naive_preprocess", "lca_naive_query",
            "lca_preprocess_ex", "etl_trim", "etl_pool_stats", "two_edge_cc", "find_bridges_hybrid", "etl_profile_enable", "etl_profile_reset",
-           "etl_profile_count", "etl_profile_get", "etl_launch_count", "etl_tune_set", "etl_tune_get")
+           "etl_profile_count", "etl_profile_get", "etl_launch_count", "etl_tune_set", "etl_tune_get",
+           "etl_workspace_size", "etl_workspace_size_batch", "etl_list_rank_ws", "lca_preprocess_ws",
+           "lca_preprocess_batch_ws", "find_bridges_ws", "find_bridges_batch_ws", "etl_status_get",
+           "etl_alloc_count", "etl_probe_gather_scatter")
+WS_KINDS = {"list_rank": 1, "lca_preprocess": 2, "lca_query": 3, "find_bridges": 4}
 TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
              "rmq_levels_per_pass": 5, "rmq_block": 6, "cc_first_slice": 7,
              "rmq_blocked": 8, "sort_rounds": 9, "cc_doubling": 10,
@@ -95,6 +99,17 @@ def load_library(path: str | None = None):
         lib.etl_profile_count.argtypes = [ctypes.POINTER(i32)]
         lib.etl_profile_get.argtypes = [i32, ctypes.c_char_p, i32, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i64)]
+        SZ = ctypes.c_size_t
+        lib.etl_workspace_size.argtypes = [i32, i64, i64, ctypes.POINTER(SZ)]
+        lib.etl_workspace_size_batch.argtypes = [i32, i32, i64, i64, ctypes.POINTER(SZ)]
+        lib.etl_list_rank_ws.argtypes = [P, i64, i32, P, P, P, SZ, P]
+        lib.lca_preprocess_ws.argtypes = [P, i32, P, SZ, P, PP]
+        lib.lca_preprocess_batch_ws.argtypes = [P, P, i32, i32, i32, P, SZ, P, PP]
+        lib.find_bridges_ws.argtypes = [P, i64, i32, P, P, P, SZ, P]
+        lib.find_bridges_batch_ws.argtypes = [P, P, P, i32, i64, i32, P, P, P, SZ, P]
+        lib.etl_status_get.argtypes = [P, P, ctypes.POINTER(i32)]
+        lib.etl_alloc_count.argtypes = [ctypes.POINTER(i64)]
+        lib.etl_probe_gather_scatter.argtypes = [P, P, i64, P, P]
         for f in EXPORTS[1:]:
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -128,13 +143,76 @@ def new_status(device=None) -> torch.Tensor:
     return torch.zeros(1, dtype=torch.int32, device=device or "cuda")
 
 
-def list_rank(succ: torch.Tensor, head: int, status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """rank[e] = distance of element e from ``head`` along ``succ`` (-1 = end)."""
+def _workspace(ws) -> tuple[int, int]:
+    """(pointer, bytes) of a caller-owned device workspace (any contiguous CUDA tensor)."""
+    if not isinstance(ws, torch.Tensor) or not ws.is_cuda or not ws.is_contiguous():
+        raise TypeError("workspace must be a contiguous CUDA tensor")
+    return ws.data_ptr(), ws.numel() * ws.element_size()
+
+
+def workspace_size(kind: str, n: int, m_or_q: int = 0) -> int:
+    """Bytes of caller-owned workspace a ``workspace=`` call of this kind needs (exact, for the tuning
+    parameters in force); kind is one of WS_KINDS."""
+    b = ctypes.c_size_t(0)
+    _check("etl_workspace_size", load_library().etl_workspace_size(WS_KINDS[kind], int(n), int(m_or_q),
+                                                                   ctypes.byref(b)))
+    return b.value
+
+
+def workspace_size_batch(kind: str, k: int, total_n: int, max_n_or_total_m: int) -> int:
+    """Workspace bytes of a batched call: kind "lca_preprocess" (third size = max_n) or "find_bridges"
+    (third size = total_m)."""
+    b = ctypes.c_size_t(0)
+    _check("etl_workspace_size_batch", load_library().etl_workspace_size_batch(
+        WS_KINDS[kind], int(k), int(total_n), int(max_n_or_total_m), ctypes.byref(b)))
+    return b.value
+
+
+def new_workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A device buffer of at least nbytes bytes to pass as ``workspace=``."""
+    return torch.empty(max(1, int(nbytes)), dtype=torch.uint8, device=device or "cuda")
+
+
+def probe_gather_scatter(order: torch.Tensor, succ: torch.Tensor, out: torch.Tensor, stream=None):
+    """Measurement aid: out[order[i]] = (succ[order[i]], i) with independent random accesses (the
+    access pattern of the ranking walk without its dependent chain); out is int32[2n] or int64[n]."""
+    if out.numel() * out.element_size() < 8 * order.numel() or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA tensor of 8 bytes per element")
+    if succ.numel() < order.numel():
+        raise ValueError("succ must have at least as many entries as order")
+    _check("etl_probe_gather_scatter", load_library().etl_probe_gather_scatter(
+        _dev_i32(order, "order"), _dev_i32(succ, "succ"), order.numel(), out.data_ptr(), _stream(stream)))
+
+
+def alloc_count() -> int:
+    """Device allocations the library has requested so far (workspace carving excluded)."""
+    c = ctypes.c_int64(0)
+    _check("etl_alloc_count", load_library().etl_alloc_count(ctypes.byref(c)))
+    return c.value
+
+
+def status_get(status: torch.Tensor, stream=None) -> int:
+    """Waits for the stream, then reads a device status word."""
+    v = ctypes.c_int32(-1)
+    _check("etl_status_get", load_library().etl_status_get(_stream(stream), _dev_i32(status, "status"),
+                                                           ctypes.byref(v)))
+    return v.value
+
+
+def list_rank(succ: torch.Tensor, head: int, status: torch.Tensor | None = None, stream=None,
+              workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """rank[e] = distance of element e from ``head`` along ``succ`` (-1 = end). With ``workspace``
+    (a device buffer of workspace_size("list_rank", len) bytes) the call allocates nothing."""
     lib = load_library()
     p = _dev_i32(succ, "succ")
     rank = torch.empty_like(succ)
-    _check("etl_list_rank", lib.etl_list_rank(p, succ.numel(), int(head), rank.data_ptr(), _status_ptr(status),
-                                              _stream(stream)))
+    if workspace is None:
+        _check("etl_list_rank", lib.etl_list_rank(p, succ.numel(), int(head), rank.data_ptr(), _status_ptr(status),
+                                                  _stream(stream)))
+    else:
+        wp, wb = _workspace(workspace)
+        _check("etl_list_rank_ws", lib.etl_list_rank_ws(p, succ.numel(), int(head), rank.data_ptr(),
+                                                        _status_ptr(status), wp, wb, _stream(stream)))
     return rank
 
 
@@ -142,7 +220,7 @@ class Lca:
     """A preprocessed tree, or a batch of trees: wraps an ``etl_lca_t`` handle."""
 
     def __init__(self, parent: torch.Tensor, stream=None, node_off: torch.Tensor | None = None,
-                 max_n: int | None = None, methods: tuple = ("rmq",)):
+                 max_n: int | None = None, methods: tuple = ("rmq",), workspace: torch.Tensor | None = None):
         lib = load_library()
         self._lib = lib
         _dev_i32(parent, "parent")  # refuse host tensors before touching any stream
@@ -150,6 +228,22 @@ class Lca:
         self.batched = node_off is not None
         self._h = ctypes.c_void_p()
         self._stream = _stream(stream)
+        if workspace is not None:
+            # the handle's tables live in the caller's workspace, which this object keeps alive
+            if tuple(methods) != ("rmq",):
+                raise ValueError("a handle in a caller-owned workspace holds the RMQ structure only")
+            wp, wb = _workspace(workspace)
+            if self.batched:
+                self.k = node_off.numel() - 1
+                _check("lca_preprocess_batch_ws", lib.lca_preprocess_batch_ws(
+                    _dev_i32(parent, "parent"), _dev_i32(node_off, "node_off"), self.k, self.n,
+                    int(max_n if max_n is not None else self.n), wp, wb, self._stream, ctypes.byref(self._h)))
+            else:
+                self.k = 1
+                _check("lca_preprocess_ws", lib.lca_preprocess_ws(_dev_i32(parent, "parent"), self.n, wp, wb,
+                                                                  self._stream, ctypes.byref(self._h)))
+            self._refs = (parent, node_off, workspace)
+            return
         if self.batched:
             self.k = node_off.numel() - 1
             _check("lca_preprocess_batch", lib.lca_preprocess_batch(
@@ -290,10 +384,12 @@ def profile_read() -> dict:
     return out
 
 
-def lca_preprocess(parent: torch.Tensor, stream=None, methods: tuple = ("rmq",)) -> Lca:
+def lca_preprocess(parent: torch.Tensor, stream=None, methods: tuple = ("rmq",),
+                   workspace: torch.Tensor | None = None) -> Lca:
     """Preprocess one tree; methods: any of "rmq" (query), "inlabel" (query_inlabel) and "tour_rmq"
-    (query_tour)."""
-    return Lca(parent, stream, methods=methods)
+    (query_tour). With ``workspace`` (workspace_size("lca_preprocess", n) bytes; RMQ only) nothing is
+    allocated and the handle's tables live in that buffer."""
+    return Lca(parent, stream, methods=methods, workspace=workspace)
 
 
 def pool_stats() -> dict:
@@ -308,9 +404,10 @@ def trim():
     _check("etl_trim", load_library().etl_trim())
 
 
-def lca_preprocess_batch(parent: torch.Tensor, node_off: torch.Tensor, max_n: int, stream=None) -> Lca:
+def lca_preprocess_batch(parent: torch.Tensor, node_off: torch.Tensor, max_n: int, stream=None,
+                         workspace: torch.Tensor | None = None) -> Lca:
     """Trees concatenated in local ids; node_off (device int32[k+1]) delimits them."""
-    return Lca(parent, stream, node_off=node_off, max_n=max_n)
+    return Lca(parent, stream, node_off=node_off, max_n=max_n, workspace=workspace)
 
 
 class NaiveLca:
@@ -335,7 +432,8 @@ class NaiveLca:
 
 
 def find_bridges_batch(edges: torch.Tensor, edge_off: torch.Tensor, node_off: torch.Tensor, total_n: int,
-                       status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                       status: torch.Tensor | None = None, stream=None,
+                       workspace: torch.Tensor | None = None) -> torch.Tensor:
     """Bridge masks of k graphs concatenated in local ids (edge_off / node_off: device int32[k+1],
     total_n = node_off[k] given by the caller so that nothing is read back from the device)."""
     lib = load_library()
@@ -344,17 +442,26 @@ def find_bridges_batch(edges: torch.Tensor, edge_off: torch.Tensor, node_off: to
     k = node_off.numel() - 1
     m = edges.shape[0]
     mask = torch.empty(m, dtype=torch.uint8, device=edges.device)
-    _check("find_bridges_batch", lib.find_bridges_batch(_dev_i32(edges, "edges"), _dev_i32(edge_off, "edge_off"),
-                                                        _dev_i32(node_off, "node_off"), k, m, total_n,
-                                                        mask.data_ptr(), _status_ptr(status), _stream(stream)))
+    if workspace is None:
+        _check("find_bridges_batch", lib.find_bridges_batch(
+            _dev_i32(edges, "edges"), _dev_i32(edge_off, "edge_off"), _dev_i32(node_off, "node_off"), k, m, total_n,
+            mask.data_ptr(), _status_ptr(status), _stream(stream)))
+    else:
+        wp, wb = _workspace(workspace)
+        _check("find_bridges_batch_ws", lib.find_bridges_batch_ws(
+            _dev_i32(edges, "edges"), _dev_i32(edge_off, "edge_off"), _dev_i32(node_off, "node_off"), k, m, total_n,
+            mask.data_ptr(), _status_ptr(status), wp, wb, _stream(stream)))
     return mask
 
 
 def find_bridges(edges: torch.Tensor, n: int, status: torch.Tensor | None = None, stream=None,
-                 method: str = "tv", out: torch.Tensor | None = None) -> torch.Tensor:
+                 method: str = "tv", out: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None) -> torch.Tensor:
     """uint8 mask, 1 for every bridge of the undirected multigraph (m, 2).
     method: "tv" (Tarjan-Vishkin low/high) or "hybrid" (tour levels + Chaitanya-Kothapalli marking).
-    out: optional contiguous uint8 device tensor of m entries to write the mask into."""
+    out: optional contiguous uint8 device tensor of m entries to write the mask into.
+    workspace: a device buffer of workspace_size("find_bridges", n, m) bytes ("tv" only): nothing is
+    allocated."""
     lib = load_library()
     if edges.dim() != 2 or edges.shape[1] != 2:
         raise ValueError("edges must have shape (m, 2)")
@@ -365,6 +472,13 @@ def find_bridges(edges: torch.Tensor, n: int, status: torch.Tensor | None = None
         if out.dtype != torch.uint8 or out.numel() != m or not out.is_contiguous() or out.device != edges.device:
             raise ValueError("out must be a contiguous uint8 tensor of m entries on the edges' device")
         mask = out
+    if workspace is not None:
+        if method != "tv":
+            raise ValueError("a caller-owned workspace is supported by the Tarjan-Vishkin method only")
+        wp, wb = _workspace(workspace)
+        _check("find_bridges_ws", lib.find_bridges_ws(_dev_i32(edges, "edges"), m, int(n), mask.data_ptr(),
+                                                      _status_ptr(status), wp, wb, _stream(stream)))
+        return mask
     fn = {"tv": lib.find_bridges, "hybrid": lib.find_bridges_hybrid}[method]
     _check("find_bridges", fn(_dev_i32(edges, "edges"), m, int(n), mask.data_ptr(), _status_ptr(status),
                               _stream(stream)))

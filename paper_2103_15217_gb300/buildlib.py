@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libetl.so")
 
 SOURCES = ["api.cu", "profile.cu", "scan.cu", "sort.cu", "rank.cu", "rmq.cu", "lca.cu", "inlabel.cu", "tour_rmq.cu", "naive.cu",
-           "bridges.cu"]
+           "bridges.cu", "workspace.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 

@@ -1,4 +1,5 @@
 // Shared host helpers and the generic list-ranking entry point.
+#include <atomic>
 #include <mutex>
 
 #include "etl_internal.cuh"
@@ -23,9 +24,39 @@ int num_sms() {
 namespace {
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[64] = {nullptr};
+std::atomic<int64_t> g_allocs{0};
+thread_local Arena *t_arena = nullptr;
+// placeholder addresses handed out while measuring: never dereferenced (the kernels are only captured)
+constexpr uintptr_t kMeasureBase = uintptr_t(1) << 40;
+
+cudaError_t arena_take(Arena *a, void **p, size_t bytes) {
+    const uintptr_t base = a->measure ? kMeasureBase : reinterpret_cast<uintptr_t>(a->base);
+    const uintptr_t at = (base + a->used + 255) & ~uintptr_t(255);
+    const size_t end = size_t(at - base) + bytes;
+    if (!a->measure && end > a->cap) return cudaErrorMemoryAllocation;
+    a->used = end;
+    *p = reinterpret_cast<void *>(at);
+    return cudaSuccess;
+}
 }  // namespace
 
+Arena *current_arena() { return t_arena; }
+ArenaScope::ArenaScope(Arena *a) : prev_(t_arena) { t_arena = a; }
+ArenaScope::~ArenaScope() { t_arena = prev_; }
+
+cudaError_t memset_async(void *p, int value, size_t bytes, cudaStream_t s) {
+    if (measuring()) return cudaSuccess;
+    return cudaMemsetAsync(p, value, bytes, s);
+}
+
+cudaError_t copy_d2d_async(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (measuring()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+}
+
 cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    if (Arena *a = t_arena) return arena_take(a, p, bytes);
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
         return cudaMallocAsync(p, bytes, s);
@@ -71,6 +102,12 @@ extern "C" etl_status etl_pool_stats(int64_t *reserved, int64_t *used) {
         return ETL_ECUDA;
     *reserved = int64_t(r);
     *used = int64_t(u);
+    return ETL_OK;
+}
+
+extern "C" etl_status etl_alloc_count(int64_t *count) {
+    if (!count) return ETL_EINVAL;
+    *count = g_allocs.load(std::memory_order_relaxed);
     return ETL_OK;
 }
 

@@ -738,7 +738,7 @@ extern "C" etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, u
     Workspace ws(s);
     int32_t *st = status ? status : ws.get<int32_t>(1);
     if (!ws.ok()) return ETL_ENOMEM;
-    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    memset_async(st, 0, sizeof(int32_t), s);
     return bridges_core(edges, m, n, is_bridge, st, ws);
 }
 
@@ -756,8 +756,8 @@ extern "C" etl_status find_bridges_batch(const int32_t *edges, const int32_t *ed
     int32_t *bad = ws.get<int32_t>(1);
     int32_t *gedges = ws.get<int32_t>(2 * total_m);
     if (!ws.ok()) return ETL_ENOMEM;
-    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
-    cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
+    memset_async(st, 0, sizeof(int32_t), s);
+    memset_async(bad, 0, sizeof(int32_t), s);
     {
         PhaseTimer pt("br.globalize", s);
         k_check_batch<<<grid_for(k, 256), 256, 0, s>>>(edge_off, node_off, k, total_m, total_n, bad, st);
@@ -779,7 +779,7 @@ extern "C" etl_status two_edge_cc(const int32_t *edges, int64_t m, int32_t n, in
     int32_t *st = status ? status : ws.get<int32_t>(1);
     uint8_t *is_bridge = ws.get<uint8_t>(m > 0 ? m : 1);
     if (!ws.ok()) return ETL_ENOMEM;
-    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    memset_async(st, 0, sizeof(int32_t), s);
     etl_status rc = m > 0 ? bridges_core(edges, m, n, is_bridge, st, ws) : ETL_OK;
     if (rc) return rc;
     const int gn = grid_for(n, 256);
@@ -807,6 +807,6 @@ extern "C" etl_status find_bridges_hybrid(const int32_t *edges, int64_t m, int32
     Workspace ws(s);
     int32_t *st = status ? status : ws.get<int32_t>(1);
     if (!ws.ok()) return ETL_ENOMEM;
-    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    memset_async(st, 0, sizeof(int32_t), s);
     return bridges_core(edges, m, n, is_bridge, st, ws, true);
 }

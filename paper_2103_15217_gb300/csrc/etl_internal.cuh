@@ -20,19 +20,55 @@ constexpr unsigned kFull = 0xffffffffu;
 // Number of SMs of the current device (cached per device).
 int num_sms();
 
+// Caller-owned device memory. While an ArenaScope is active on the calling
+// thread, every device allocation the library makes (dev_alloc, and so
+// Workspace::get and the tables of an LCA handle) is carved from the arena
+// instead of the allocator: 256-byte aligned, never freed, never reused within
+// the call. A measuring arena has no memory behind it: it hands out placeholder
+// addresses and only counts bytes; it is used with a stream under capture, so
+// the kernels that receive those addresses are recorded and never run, and the
+// async memset / copy helpers below skip their work.
+struct Arena {
+    char *base = nullptr;  // caller's memory (null while measuring)
+    size_t cap = 0;        // bytes available from base
+    size_t used = 0;       // bytes handed out so far (alignment included)
+    bool measure = false;
+};
+Arena *current_arena();
+class ArenaScope {
+  public:
+    explicit ArenaScope(Arena *a);
+    ~ArenaScope();
+    ArenaScope(const ArenaScope &) = delete;
+    ArenaScope &operator=(const ArenaScope &) = delete;
+
+  private:
+    Arena *prev_;
+};
+inline bool measuring() {
+    const Arena *a = current_arena();
+    return a && a->measure;
+}
+
 // Stream-ordered device allocation from the library's own per-device memory
 // pool, which keeps freed memory reserved (release threshold = max) so that
 // repeated calls do not pay for re-mapping, and never reuses a block freed on
 // another stream by making this stream wait for that one; while the stream is
 // being captured into a graph the default pool is used (graph memory nodes).
-// Freed with cudaFreeAsync. Returns cudaSuccess or the allocator's error.
+// Freed with cudaFreeAsync. Inside an ArenaScope the memory comes from the
+// arena instead (and must not be freed). Returns cudaSuccess or the
+// allocator's error (cudaErrorMemoryAllocation when the arena is too small).
 cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
+
+// cudaMemsetAsync / device-to-device cudaMemcpyAsync, skipped while measuring
+cudaError_t memset_async(void *p, int value, size_t bytes, cudaStream_t s);
+cudaError_t copy_d2d_async(void *dst, const void *src, size_t bytes, cudaStream_t s);
 
 // Stream-ordered scratch: every buffer taken here is released with
 // cudaFreeAsync on the same stream when the Workspace goes out of scope.
 class Workspace {
   public:
-    explicit Workspace(cudaStream_t s) : s_(s) {}
+    explicit Workspace(cudaStream_t s) : s_(s), arena_(current_arena() != nullptr) {}
     ~Workspace() { release(); }
     Workspace(const Workspace &) = delete;
     Workspace &operator=(const Workspace &) = delete;
@@ -50,7 +86,8 @@ class Workspace {
     }
     bool ok() const { return ok_; }
     void release() {
-        for (void *p : bufs_) cudaFreeAsync(p, s_);
+        if (!arena_)
+            for (void *p : bufs_) cudaFreeAsync(p, s_);
         bufs_.clear();
     }
     cudaStream_t stream() const { return s_; }
@@ -59,6 +96,7 @@ class Workspace {
     cudaStream_t s_;
     std::vector<void *> bufs_;
     bool ok_ = true;
+    bool arena_;  // buffers come from a caller-owned arena: nothing to free
 };
 
 // Brackets a launch group with CUDA events when phase timing is enabled
@@ -312,4 +350,5 @@ struct etl_lca_s {
     void *tour_table = nullptr;  // Euler-tour RMQ: blocked table of (depth << 32 | node) keys over 2n positions
     int32_t *tpos = nullptr;     // Euler-tour RMQ: tour position of each node's opening bracket
     etl::BlockedLayout tbl{};
+    bool arena = false;          // device arrays live in a caller-owned workspace: lca_free frees none of them
 };

@@ -193,6 +193,7 @@ etl_status lca_build_inlabel_impl(etl_lca_t h, const int32_t *parent, cudaStream
 }
 
 extern "C" etl_status lca_build_inlabel(etl_lca_t h, const int32_t *parent, void *stream) {
+    if (h && h->arena) return ETL_EINVAL;  // a handle inside a caller's workspace takes no more tables
     return lca_build_inlabel_impl(h, parent, static_cast<cudaStream_t>(stream));
 }
 

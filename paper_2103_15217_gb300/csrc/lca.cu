@@ -359,6 +359,10 @@ int grid_for(int64_t work, int threads) {
 
 void free_handle(etl_lca_s *h) {
     if (!h) return;
+    if (h->arena) {  // the device arrays belong to the caller's workspace
+        delete h;
+        return;
+    }
     cudaStream_t s = h->stream;
     for (int32_t *p : {h->pre, h->depth, h->size, h->order, h->table, h->status, h->node_off})
         if (p) cudaFreeAsync(p, s);
@@ -372,6 +376,7 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
                      bool with_table, cudaStream_t s, etl_lca_t *out) {
     const bool batch = node_off != nullptr;
     etl_lca_s *h = new etl_lca_s;
+    h->arena = current_arena() != nullptr;
     h->n = n;
     h->k = k;
     h->stream = s;
@@ -397,8 +402,8 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
         free_handle(h);
         return ETL_ENOMEM;
     }
-    cudaMemsetAsync(h->status, 0, sizeof(int32_t), s);
-    if (batch) cudaMemcpyAsync(h->node_off, node_off, size_t(k + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    memset_async(h->status, 0, sizeof(int32_t), s);
+    if (batch) copy_d2d_async(h->node_off, node_off, size_t(k + 1) * sizeof(int32_t), s);
     etl_status st = ETL_OK;
     {
         Workspace ws(s);
@@ -412,10 +417,10 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
         if (!ws.ok()) st = ETL_ENOMEM;
         const int32_t *par = batch ? gparent : parent;
         if (!st) {
-            cudaMemsetAsync(cnt, 0, nb, s);
-            cudaMemsetAsync(misc, 0, 4 * sizeof(int32_t), s);
-            cudaMemsetAsync(root_cnt, 0, size_t(k) * sizeof(int32_t), s);
-            cudaMemsetAsync(root_of, 0, size_t(k) * sizeof(int32_t), s);
+            memset_async(cnt, 0, nb, s);
+            memset_async(misc, 0, 4 * sizeof(int32_t), s);
+            memset_async(root_cnt, 0, size_t(k) * sizeof(int32_t), s);
+            memset_async(root_of, 0, size_t(k) * sizeof(int32_t), s);
             PhaseTimer pt("lca.count", s);
             if (batch) {
                 k_check_offsets<<<grid_for(k, 256), 256, 0, s>>>(h->node_off, k, n, misc + 1, h->status);
@@ -591,7 +596,7 @@ extern "C" etl_status lca_export(etl_lca_t h, int32_t *pre, int32_t *depth, int3
     int32_t *dst[4] = {pre, depth, size, order};
     const int32_t *src[4] = {h->pre, h->depth, h->size, h->order};
     for (int i = 0; i < 4; ++i)
-        if (dst[i] && cudaMemcpyAsync(dst[i], src[i], nb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return ETL_ECUDA;
+        if (dst[i] && copy_d2d_async(dst[i], src[i], nb, s) != cudaSuccess) return ETL_ECUDA;
     return ETL_OK;
 }
 

@@ -138,8 +138,8 @@ extern "C" etl_status lca_naive_preprocess(const int32_t *parent, int32_t n, int
     int32_t *cnt = ws.get<int32_t>(2);  // [0] roots, [1] nodes still pending after the last launch
     int32_t *st = status ? status : ws.get<int32_t>(1);
     if (!ws.ok()) return ETL_ENOMEM;
-    cudaMemsetAsync(st, 0, sizeof(int32_t), s);
-    cudaMemsetAsync(cnt, 0, 2 * sizeof(int32_t), s);
+    memset_async(st, 0, sizeof(int32_t), s);
+    memset_async(cnt, 0, 2 * sizeof(int32_t), s);
     const int g = grid_for(n, 256);
     PhaseTimer pt("naive.levels", s);
     k_naive_init<<<g, 256, 0, s>>>(parent, n, ad, level, cnt, st);
@@ -149,7 +149,7 @@ extern "C" etl_status lca_naive_preprocess(const int32_t *parent, int32_t n, int
     int launches = 1;
     for (double c = 1; c < double(n); c *= (kJumpsPerLaunch + 1)) ++launches;
     for (int r = 0; r < launches; ++r) {
-        if (r == launches - 1) cudaMemsetAsync(cnt + 1, 0, sizeof(int32_t), s);
+        if (r == launches - 1) memset_async(cnt + 1, 0, sizeof(int32_t), s);
         k_naive_jump<<<g, 256, 0, s>>>(n, ad, level, cnt + 1);
         note_launch();
     }

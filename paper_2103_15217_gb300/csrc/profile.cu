@@ -72,12 +72,50 @@ PhaseTimer::~PhaseTimer() {
     g_recs.push_back(Rec{name_, static_cast<cudaEvent_t>(a_), static_cast<cudaEvent_t>(b_)});
 }
 
+// Measurement aid: the access pattern of one step of the ranking walk (read the successor of a
+// random element, write an 8-byte record at the same random index) without the walk's chain of
+// dependent loads: element i of a random permutation is visited by thread i, so every gather is
+// independent and the memory system sees as many as it can take. Its rate is the ceiling of any
+// walk over a list in random order. Indices outside [0, n) are skipped.
+__global__ void k_probe_gather_scatter(const int32_t *__restrict__ order, const int32_t *__restrict__ succ,
+                                       int64_t n, uint2 *__restrict__ out) {
+    constexpr int kIlp = 4;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t base = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; base < n; base += stride * kIlp) {
+        int32_t j[kIlp], x[kIlp];
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            const int64_t i = base + k * stride;
+            j[k] = i < n ? __ldcs(order + i) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) x[k] = (j[k] >= 0 && j[k] < n) ? __ldg(succ + j[k]) : 0;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k)
+            if (j[k] >= 0 && j[k] < n) out[j[k]] = make_uint2(uint32_t(x[k]), uint32_t(base + k * stride));
+    }
+}
+
 std::atomic<int64_t> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launch() {
+    if (!measuring()) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 }  // namespace etl
 
 using namespace etl;
+
+extern "C" etl_status etl_probe_gather_scatter(const int32_t *order, const int32_t *succ, int64_t n, void *out,
+                                                void *stream) {
+    if (!order || !succ || !out || n < 1 || n > int64_t(INT32_MAX)) return ETL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t blocks = ceil_div(ceil_div(n, 4), 256);
+    const int64_t cap = int64_t(num_sms()) * 8 * 4;  // four waves of full occupancy
+    if (blocks > cap) blocks = cap;
+    k_probe_gather_scatter<<<int(blocks), 256, 0, s>>>(order, succ, n, static_cast<uint2 *>(out));
+    note_launch();
+    return last_launch();
+}
 
 extern "C" etl_status etl_launch_count(int64_t *count) {
     if (!count) return ETL_EINVAL;

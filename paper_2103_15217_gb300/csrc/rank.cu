@@ -385,7 +385,7 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
     int32_t *ctr = ws.get<int32_t>(2);
     int32_t *head1 = ws.get<int32_t>(1);
     if (!ws.ok()) return ETL_ENOMEM;
-    cudaMemsetAsync(ctr, 0, 2 * sizeof(int32_t), s);
+    memset_async(ctr, 0, 2 * sizeof(int32_t), s);
     etl_status st;
     {
         PhaseTimer pt0("rank.walk0", s);
@@ -421,8 +421,8 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
         int32_t *nn = ws.get<int32_t>(ncap), *n1 = ws.get<int32_t>(ncap), *n2 = ws.get<int32_t>(ncap);
         int32_t *c = ws.get<int32_t>(2), *hd = ws.get<int32_t>(1);
         if (!ws.ok()) return ETL_ENOMEM;
-        cudaMemsetAsync(c, 0, 2 * sizeof(int32_t), s);
-        cudaMemsetAsync(L.loc, 0xff, size_t(L.cap) * sizeof(int4), s);
+        memset_async(c, 0, 2 * sizeof(int32_t), s);
+        memset_async(L.loc, 0xff, size_t(L.cap) * sizeof(int4), s);
         {
             PhaseTimer ptw("rank.walk", s);
             const int grid = walk_grid(L.cap, 28, P);

@@ -93,7 +93,7 @@ template <class T>
 etl_status scan_impl(const T *in, int32_t *out, int64_t n, const int32_t *d_n, Workspace &ws) {
     cudaStream_t s = ws.stream();
     if (n <= 0) {
-        cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+        memset_async(out, 0, sizeof(int32_t), s);
         return last_launch();
     }
     int64_t nb = ceil_div(n, kTile);

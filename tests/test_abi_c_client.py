@@ -23,6 +23,15 @@ CHECKS = r"""
     if (etl_tune_get(999, &v) != ETL_EINVAL) return 17;
     if (strcmp(etl_status_string(ETL_EBADTREE), "ETL_EBADTREE") != 0) return 18;
     if (strcmp(etl_status_string(ETL_ETIMEOUT), "ETL_ETIMEOUT") != 0) return 19;
+    {
+        size_t b = 1;
+        if (etl_workspace_size(99, 10, 10, &b) != ETL_EINVAL || b != 0) return 20;
+        if (etl_workspace_size(ETL_WS_LCA_QUERY, 10, 5, &b) != ETL_OK || b != 0) return 21;
+        if (lca_preprocess_ws((const int32_t *)16, 5, NULL, 1024, NULL, &h) != ETL_EINVAL) return 22;
+        if (find_bridges_ws((const int32_t *)16, 3, 4, (uint8_t *)16, NULL, NULL, 1024, NULL) != ETL_EINVAL)
+            return 23;
+        if (etl_status_get(NULL, NULL, &v) != ETL_EINVAL) return 24;
+    }
     puts("ok");
     return 0;
 """

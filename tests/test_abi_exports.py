@@ -58,6 +58,7 @@ def test_host_side_validation(lib):
     assert lib.lca_free(None) == 0
     big = 1 << 30  # one past the largest tree (2^30 - 1 nodes: two list elements per node in 31 bits)
     assert lib.lca_preprocess(ctypes.c_void_p(16), big, None, ctypes.byref(h)) == 1
+
     for flags in (0, 8, 16, -1):  # no method, or an unknown bit
         assert lib.lca_preprocess_ex(ctypes.c_void_p(16), 5, flags, None, ctypes.byref(h)) == 1
     assert lib.lca_preprocess_ex(ctypes.c_void_p(16), big, 1, None, ctypes.byref(h)) == 1
@@ -94,3 +95,29 @@ def test_product_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "etl_oracle" not in src, f
+
+
+def test_workspace_entry_points_validate_on_the_host(lib):
+    # refused before any CUDA call: unknown kinds, sizes out of range, a missing workspace
+    b = ctypes.c_size_t(123)
+    assert lib.etl_workspace_size(99, 10, 10, ctypes.byref(b)) == 1 and b.value == 0
+    assert lib.etl_workspace_size(2, 0, 0, ctypes.byref(b)) == 1              # n < 1
+    assert lib.etl_workspace_size(4, 10, -1, ctypes.byref(b)) == 1            # m < 0
+    assert lib.etl_workspace_size(3, 10, 5, ctypes.byref(b)) == 0 and b.value == 0   # queries: no scratch
+    assert lib.etl_workspace_size(2, 10, 0, None) == 1
+    assert lib.etl_workspace_size_batch(2, 0, 10, 5, ctypes.byref(b)) == 1     # k < 1
+    assert lib.etl_workspace_size_batch(2, 3, 10, 11, ctypes.byref(b)) == 1    # max_n > total_n
+    h = ctypes.c_void_p(77)
+    assert lib.lca_preprocess_ws(ctypes.c_void_p(16), 5, None, 1 << 20, None, ctypes.byref(h)) == 1
+    assert h.value is None                                                    # *out cleared
+    assert lib.etl_list_rank_ws(ctypes.c_void_p(16), 4, 0, ctypes.c_void_p(16), None, None, 1 << 20, None) == 1
+    assert lib.find_bridges_ws(ctypes.c_void_p(16), 3, 4, ctypes.c_void_p(16), None, None, 1 << 20, None) == 1
+    assert lib.find_bridges_batch_ws(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 3, 4,
+                                     ctypes.c_void_p(16), None, None, 1 << 20, None) == 1
+    assert lib.lca_preprocess_batch_ws(ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 5, 5, None, 1 << 20, None,
+                                       ctypes.byref(h)) == 1
+    v = ctypes.c_int32(0)
+    assert lib.etl_status_get(None, None, ctypes.byref(v)) == 1
+    c = ctypes.c_int64(-1)
+    assert lib.etl_alloc_count(ctypes.byref(c)) == 0 and c.value >= 0
+    assert lib.etl_alloc_count(None) == 1
