@@ -1,12 +1,15 @@
 """Autotuner for the launch parameters of the Euler-tour library.
 
 The knobs change no result, only speed (``etl_tune_set``): the list ranker's
-splitter densities and walk-kernel shape, the range tables' form and build
-shape, the radix passes' tile size and ranking, and the connectivity pass's
-hooking schedule. ``autotune`` times candidate settings with CUDA events on
-representative inputs -- a tree preprocessing (tour + ranking + range table)
-and a bridge-finding call of the requested size -- and keeps the fastest. Results are cached per (GPU name, size bucket) in
-``_build/tune_cache.json`` so later runs start from the tuned values.
+splitter densities and walk-kernel shape (threads per block and resident
+blocks per SM of the walks over lists larger than L2), the range tables'
+form and build shape, the radix passes' tile size and ranking, and the
+connectivity pass's hooking schedule. ``autotune`` times candidate settings
+with CUDA events on the caller's own work -- a callable that enqueues one
+representative run (for example one batch of trees and graphs of the mix to
+be served), with its inputs already on the device -- and keeps the fastest.
+Results are cached per (GPU name, caller's key) in ``_build/tune_cache.json``
+so later runs start from the tuned values.
 
 The search is coordinate-wise: ranking density first (it sets the length of
 the longest dependent walk), then the walk kernel's shape, then the other
@@ -17,13 +20,12 @@ moving on.
 from __future__ import annotations
 
 import json
-import math
 import os
 import statistics
 
 import torch
 
-from . import find_bridges, lca_preprocess, load_library, tune_get, tune_set
+from . import load_library, tune_get, tune_set
 
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json")
 
@@ -43,12 +45,8 @@ SPACE = [
 ]
 
 
-def _bucket(n: int) -> str:
-    return f"2^{max(10, int(math.ceil(math.log2(max(n, 2)))))}"
-
-
-def _key(n: int) -> str:
-    return f"{torch.cuda.get_device_name()}|{_bucket(n)}"
+def _key(key: str) -> str:
+    return f"{torch.cuda.get_device_name()}|{key}"
 
 
 def _load_cache() -> dict:
@@ -65,19 +63,6 @@ def _save_cache(c: dict):
     with open(tmp, "w") as f:
         json.dump(c, f, indent=1, sort_keys=True)
     os.replace(tmp, _CACHE)
-
-
-def _inputs(n: int, seed: int = 7):
-    import sys
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
-    import synth
-    dev = torch.device("cuda", torch.cuda.current_device())
-    parent = torch.from_numpy(synth.tree_parent(n, None, seed=seed)).to(dev)
-    gn = max(64, n // 4)
-    edges = torch.from_numpy(synth.easy_graph(gn, 8 * gn, seed=seed)).to(dev)
-    return parent, edges, gn
 
 
 def _time(fn, reps: int) -> float:
@@ -122,21 +107,17 @@ def coordinate_search(space, start: dict, measure, is_valid=lambda p: True):
     return best, best_t, trials
 
 
-def autotune(n: int = 1 << 22, reps: int = 3, use_cache: bool = True, verbose: bool = False) -> dict:
-    """Tune for trees of about n nodes (and graphs of n/4 nodes, 8 edges per node).
-    Applies the best setting and returns {"params": ..., "ms": ..., "trials": ...}."""
+def autotune(workload, key: str, reps: int = 3, use_cache: bool = True, verbose: bool = False,
+             space=SPACE) -> dict:
+    """Tune on the caller's work: workload() enqueues one representative run on the current stream
+    (inputs already on the device; every call must do the same work). key names the workload in the
+    cache. Applies the best setting and returns {"params", "ms", "default_ms", "trials"}."""
     load_library()
-    key = _key(n)
+    ckey = _key(key)
     cache = _load_cache() if use_cache else {}
-    if key in cache:
-        tune_set(**cache[key]["params"])
-        return dict(cache[key], cached=True)
-    parent, edges, gn = _inputs(n)
-
-    def workload():
-        h = lca_preprocess(parent)
-        h.free()
-        find_bridges(edges, gn)
+    if ckey in cache:
+        tune_set(**cache[ckey]["params"])
+        return dict(cache[ckey], cached=True)
 
     def measure(params):
         try:
@@ -148,16 +129,9 @@ def autotune(n: int = 1 << 22, reps: int = 3, use_cache: bool = True, verbose: b
             print(f"  {params}: {ms:.3f} ms")
         return ms
 
-    best, best_ms, trials = coordinate_search(SPACE, tune_get(), measure, valid)
+    best, best_ms, trials = coordinate_search(space, tune_get(), measure, valid)
     tune_set(**best)
-    res = {"params": best, "ms": best_ms, "n": n, "trials": len(trials),
-           "default_ms": trials[0][1]}
-    cache[key] = res
+    res = {"params": best, "ms": best_ms, "key": key, "trials": len(trials), "default_ms": trials[0][1]}
+    cache[ckey] = res
     _save_cache(cache)
     return res
-
-
-if __name__ == "__main__":
-    import sys
-    n = int(sys.argv[1]) if len(sys.argv) > 1 else 1 << 22
-    print(json.dumps(autotune(n, use_cache=False, verbose=True)))

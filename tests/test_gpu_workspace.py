@@ -182,3 +182,33 @@ def test_short_workspace_is_refused():
     h = etl.lca_preprocess(dev(parent), workspace=ws)  # the exact size is enough
     assert h.status() == 0
     h.free()
+
+
+def test_data_errors_in_workspace():
+    # malformed inputs through the _ws entry points: the same device status codes and outputs as the
+    # plain calls (not one tree -> ETL_EBADTREE and -1 answers; endpoint out of range -> ETL_EBADGRAPH
+    # and an all-zero mask), and nothing allocated
+    etl = _etl()
+    u = dev(np.array([0, 1, 2], np.int32))
+    a0 = etl.alloc_count()
+    for parent in ([-1, -1, 0], [-1, 2, 1], [-1, 7, 0], [1, 0, 0]):
+        ws = etl.new_workspace(etl.workspace_size("lca_preprocess", len(parent)))
+        h = etl.lca_preprocess(dev(np.array(parent, np.int32)), workspace=ws)
+        assert h.status() == 4
+        assert (host(h.query(u, u)) == -1).all()
+        h.free()
+    n = 50000   # a long cycle hidden in a big tree
+    parent = synth.tree_parent(n, None, seed=3)
+    kids = np.nonzero(parent >= 0)[0]
+    parent[kids[10]], parent[kids[20]] = kids[20], kids[10]
+    ws = etl.new_workspace(etl.workspace_size("lca_preprocess", n))
+    h = etl.lca_preprocess(dev(parent), workspace=ws)
+    assert h.status() == 4
+    h.free()
+    e = np.array([[0, 1], [1, 4], [2, 3]], np.int32)
+    ws = etl.new_workspace(etl.workspace_size("find_bridges", 4, 3))
+    st = etl.new_status()
+    mask = host(etl.find_bridges(dev(e), 4, status=st, workspace=ws))
+    assert etl.status_get(st) == 6 and (mask == 0).all()
+    assert etl.alloc_count() == a0
+
