@@ -268,7 +268,12 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  * (paper_2103_15217_gb300/tune.py). Process-wide; set them between calls,
  * not while calls are being enqueued from another thread.
  *   ETL_TUNE_RANK_K0_LOG2   level-0 splitter density of the list ranker: one
- *                           splitter per 2^k elements, k in [1, 8] (default 5)
+ *                           splitter per 2^k elements, k in [1, 8] (default 5),
+ *                           for lists of more than 2^22 elements; shorter
+ *                           lists (bound by the latency of their longest
+ *                           sublist) take one in 4 up to 2^15 elements, one in
+ *                           8 up to 2^20, one in 16 up to 2^22, or this value
+ *                           where it is denser
  *   ETL_TUNE_RANK_K_LOG2    density at the upper ranking levels, [1, 8] (4)
  *   ETL_TUNE_RANK_BLOCK     threads per block of the walk kernels, one of
  *                           64, 128, 256, 512, 1024 (128)

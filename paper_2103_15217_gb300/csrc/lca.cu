@@ -103,14 +103,6 @@ __global__ void k_count_children(const int32_t *__restrict__ parent, int32_t n, 
     }
 }
 
-// exactly one root per instance; the list starts at the first root's opening bracket
-__global__ void k_check_roots(const int32_t *__restrict__ root_cnt, const int32_t *__restrict__ root_of, int32_t k,
-                              int32_t *__restrict__ head, int32_t *__restrict__ status) {
-    for (int64_t i = gtid(); i < k; i += gstride())
-        if (root_cnt[i] != 1) set_status(status, ETL_EBADTREE);
-    if (gtid() == 0) *head = 2 * root_of[0];
-}
-
 // kv[t] = (parent, child), grouped by parent with children ascending
 __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restrict__ coff, int32_t n,
                             int32_t *__restrict__ succ) {
@@ -143,9 +135,14 @@ __global__ void k_contract_leaves(const int32_t *__restrict__ coff, const int32_
     }
 }
 
-// leave root i -> enter root i+1 (or end of the list after the last tree)
-__global__ void k_link_roots(const int32_t *__restrict__ root_of, int32_t k, int32_t n, int32_t *__restrict__ succ) {
+// exactly one root per instance; leave root i -> enter root i+1 (or end of the list after the last
+// tree); the list starts at the first root's opening bracket
+__global__ void k_link_roots(const int32_t *__restrict__ root_cnt, const int32_t *__restrict__ root_of, int32_t k,
+                             int32_t n, int32_t *__restrict__ succ, int32_t *__restrict__ head,
+                             int32_t *__restrict__ status) {
+    if (gtid() == 0) *head = 2 * root_of[0];
     for (int64_t i = gtid(); i < k; i += gstride()) {
+        if (root_cnt[i] != 1) set_status(status, ETL_EBADTREE);
         const int32_t r = root_of[i];
         if (r < 0 || r >= n) continue;
         const int32_t nr = (i + 1 < k) ? root_of[i + 1] : -1;
@@ -435,8 +432,6 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
                                                                          nullptr, cnt, root_cnt, root_of, h->status);
                 note_launch();
             }
-            k_check_roots<<<grid_for(k, 256), 256, 0, s>>>(root_cnt, root_of, k, misc, h->status);
-            note_launch();
             st = last_launch();
         }
         if (!st) st = scan_exclusive_i32(cnt, coff, n, ws);
@@ -446,7 +441,7 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
             PhaseTimer pt("lca.succ", s);
             k_tour_succ<<<grid_for(n, 256), 256, 0, s>>>(sr.kv, coff, n, succ);
             note_launch();
-            k_link_roots<<<grid_for(k, 256), 256, 0, s>>>(root_of, k, n, succ);
+            k_link_roots<<<grid_for(k, 256), 256, 0, s>>>(root_cnt, root_of, k, n, succ, misc, h->status);
             note_launch();
             k_contract_leaves<<<grid_for(n, 256), 256, 0, s>>>(coff, par, n, succ);
             note_launch();

@@ -363,9 +363,25 @@ RankParams &rank_params() {
 // 19% less DRAM traffic, and faster, with 512 walkers per SM than with 2048).
 constexpr int64_t kWalkL2Bytes = int64_t(96) << 20;
 
-int walk_grid(int64_t len, int64_t bytes_per_elem, const RankParams &P) {
+// Level-0 splitter density (log2 of elements per splitter). A list longer than 2^22 elements takes
+// the tuned value (P.k0_log2): its walks are bound by DRAM traffic, which sparser splitters reduce.
+// A shorter list sits in L2 and its walk is bound by the latency of its longest sublist (about
+// 2^k * ln(len / 2^k) dependent steps), so it takes denser splitters: one in 4 up to 2^15 elements,
+// one in 8 up to 2^20, one in 16 up to 2^22, or the tuned value if that is denser (measured on
+// random recursive trees of 2^11 .. 2^22 nodes and on forest tours of 2^12 .. 2^22-node graphs).
+int level0_density(int64_t len, const RankParams &P) {
+    if (len > (int64_t(1) << 22)) return P.k0_log2;
+    const int k = len > (int64_t(1) << 20) ? 4 : len > (int64_t(1) << 15) ? 3 : 2;
+    return k < P.k0_log2 ? k : P.k0_log2;
+}
+
+// ... and never more walkers than sublists: on a short list the surplus warps would only contend for
+// the work counter before finding nothing to walk
+int walk_grid(int64_t len, int64_t bytes_per_elem, int64_t sublists, const RankParams &P) {
     const int per_sm = len * bytes_per_elem > kWalkL2Bytes ? P.blocks_per_sm : 2048 / P.block;
-    return num_sms() * (per_sm > 0 ? per_sm : 1);
+    const int64_t grid = int64_t(num_sms()) * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = ceil_div(sublists, P.block);
+    return int(need < grid ? (need > 0 ? need : 1) : grid);
 }
 
 etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, const int32_t *d_head, bool dual,
@@ -377,7 +393,7 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
 
     // ---- level 0: implicit weights, packed 16-bit local offsets
     const int64_t len0 = n_cap;
-    Hash H = make_hash(len0, P.k0_log2);
+    Hash H = make_hash(len0, level0_density(len0, P));
     int32_t dyn_cap = int32_t(len0 / kLcap + 2);
     int64_t cap1 = int64_t(H.S0) + 1 + dyn_cap;
     uint2 *packed = ws.get<uint2>(len0);
@@ -389,7 +405,7 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
     etl_status st;
     {
         PhaseTimer pt0("rank.walk0", s);
-        const int grid = walk_grid(len0, 12, P);
+        const int grid = walk_grid(len0, 12, int64_t(H.S0) + 1, P);
         if (dual)
             k_walk0<true><<<grid, P.block, 0, s>>>(succ, len0, d_head, H, packed, rnext, rw1, rw2, ctr, dyn_cap, head1,
                                                     status);
@@ -425,7 +441,7 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
         memset_async(L.loc, 0xff, size_t(L.cap) * sizeof(int4), s);
         {
             PhaseTimer ptw("rank.walk", s);
-            const int grid = walk_grid(L.cap, 28, P);
+            const int grid = walk_grid(L.cap, 28, int64_t(h.S0) + 1, P);
             k_walk<<<grid, P.block, 0, s>>>(L.succ, L.w1, L.w2, L.base, L.d_add, L.cap, L.d_head, h, L.loc, nn, n1, n2,
                                             c, dcap, hd, status);
         note_launch();

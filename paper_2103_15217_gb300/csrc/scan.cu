@@ -89,6 +89,52 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// A short input (one tile of 16384 entries at most) is scanned by one block of 1024 threads: one
+// launch instead of reduce + scan of the partials + scan of the tiles, three launches that each cost a
+// few microseconds the work itself does not need (the digit offsets of a radix pass over up to 2^19
+// elements, for instance). Longer inputs keep the three launches: a block walking several tiles one
+// after another measured slower than them.
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallWarps = kSmallThreads / kWarp;
+constexpr int64_t kSmallMax = int64_t(kSmallThreads) * kItems;
+static_assert(kSmallWarps == kWarp, "the warp totals are scanned by one warp");
+
+template <class T>
+__global__ void __launch_bounds__(kSmallThreads)
+    k_scan_small(const T *__restrict__ in, int32_t *__restrict__ out, int64_t n, const int32_t *d_n) {
+    __shared__ int32_t wsum[kSmallWarps], wpre[kSmallWarps];
+    __shared__ int32_t total;
+    const int64_t nn = eff_len<T>(n, d_n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = warp * (kWarp * kItems);
+    int32_t vals[kItems];
+    int32_t running = 0;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t idx = base + j * kWarp + lane;
+        const int32_t x = idx < nn ? int32_t(in[idx]) : 0;
+        const int32_t inc = warp_incl_scan(x, lane);
+        vals[j] = running + inc - x;
+        running += __shfl_sync(kFull, inc, 31);
+    }
+    if (lane == 0) wsum[warp] = running;
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the warps' totals (kSmallWarps == 32)
+        const int32_t w = wsum[lane];
+        const int32_t inc = warp_incl_scan(w, lane);
+        wpre[lane] = inc - w;
+        if (lane == kWarp - 1) total = inc;
+    }
+    __syncthreads();
+    const int32_t woff = wpre[warp];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t idx = base + j * kWarp + lane;
+        if (idx < n) out[idx] = vals[j] + woff;
+    }
+    if (threadIdx.x == 0) out[n] = total;
+}
+
 template <class T>
 etl_status scan_impl(const T *in, int32_t *out, int64_t n, const int32_t *d_n, Workspace &ws) {
     cudaStream_t s = ws.stream();
@@ -99,6 +145,11 @@ etl_status scan_impl(const T *in, int32_t *out, int64_t n, const int32_t *d_n, W
     int64_t nb = ceil_div(n, kTile);
     if (nb == 1) {
         k_scan_tile<T><<<1, kThreads, 0, s>>>(in, out, n, d_n, nullptr, 1);
+        note_launch();
+        return last_launch();
+    }
+    if (n <= kSmallMax) {
+        k_scan_small<T><<<1, kSmallThreads, 0, s>>>(in, out, n, d_n);
         note_launch();
         return last_launch();
     }

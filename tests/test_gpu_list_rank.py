@@ -63,6 +63,14 @@ def _rule(cap, k_log2):
     return (1 << b) - 1, 1 << (b - k_log2)
 
 
+def _level0_density(length, tuned):
+    """The ranker's level-0 density: the tuned value above 2^22 elements, denser below (one in 4 up to
+    2^15 elements, 8 up to 2^20, 16 up to 2^22, or the tuned value where that is denser)."""
+    if length > 1 << 22:
+        return tuned
+    return min(4 if length > 1 << 20 else 3 if length > 1 << 15 else 2, tuned)
+
+
 def _hashed(x, mask):
     return ((np.asarray(x, np.uint64) * np.uint64(KMUL)) & np.uint64(mask)).astype(np.int64)
 
@@ -86,7 +94,7 @@ def test_level0_walk_opens_dynamic_splitters(n):
     # every non-splitter first, then the splitters: the head's walk crosses
     # ~31/32 of the list and has to open a dynamic splitter every KLCAP elements
     import paper_2103_15217_gb300 as etl
-    k0 = etl.tune_get()["rank_k0_log2"]
+    k0 = _level0_density(n, etl.tune_get()["rank_k0_log2"])
     split = _splitter_mask(n, n, k0)
     rng = np.random.default_rng(n)
     idx = np.arange(n, dtype=np.int32)
@@ -110,7 +118,7 @@ def test_upper_level_walk_opens_dynamic_splitters(n):
     # reduced list from its head crosses ~15/16 of it
     import paper_2103_15217_gb300 as etl
     t = etl.tune_get()
-    k0, k1 = t["rank_k0_log2"], t["rank_k_log2"]
+    k0, k1 = _level0_density(n, t["rank_k0_log2"]), t["rank_k_log2"]
     mask0, s00 = _rule(n, k0)
     split0 = _hashed(np.arange(n), mask0) < s00
     cap1 = s00 + 1 + (n // KLCAP + 2)
@@ -142,7 +150,7 @@ def test_tree_tour_opens_dynamic_splitters():
     import oracle
     import paper_2103_15217_gb300 as etl
     n = 1 << 20
-    k0 = etl.tune_get()["rank_k0_log2"]
+    k0 = _level0_density(2 * n, etl.tune_get()["rank_k0_log2"])
     split = _splitter_mask(2 * n, 2 * n, k0)
     labels = np.arange(n, dtype=np.int32)
     open_split = split[2 * labels]
