@@ -10,7 +10,8 @@
 // stable scatter. Inside a tile each warp ranks its 32-element rounds (peers
 // with the same digit by __match_any_sync or by eight ballots) with per-warp
 // smem counters, so the order of equal digits is preserved without any atomics
-// on global memory.
+// on global memory; the ranked tile is staged in shared memory in digit order
+// and written out in runs.
 #include "etl_internal.cuh"
 
 namespace etl {
@@ -19,6 +20,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / kWarp;
 constexpr int kRadix = 256;
+static_assert(kThreads == kRadix, "the scatter handles one digit per thread");
 // R = 32-element rounds per warp: a tile of 8 warps holds 256 * R elements (R = 8 or 16, chosen by
 // the SORT_ROUNDS tuning knob; larger tiles give longer runs per digit in the scatter)
 
@@ -78,6 +80,9 @@ __device__ __forceinline__ unsigned digit_peers(int d, bool valid, int lane) {
     return valid ? peers : (1u << lane);
 }
 
+// The tile's elements are first placed in shared memory in digit order (stable: by digit, then by
+// position in the tile), then written out by consecutive threads: equal digits form one run of the
+// output, so a warp's store touches a few runs instead of one segment per lane.
 template <int R, bool BALLOT>
 __global__ void __launch_bounds__(kThreads)
     k_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, const int2 *__restrict__ kv,
@@ -86,6 +91,9 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int kRounds = R, kWarpTile = kWarp * R, kTile = kWarps * kWarpTile;
     __shared__ int32_t wcnt[kWarps][kRadix];
     __shared__ int32_t gbase[kRadix];
+    __shared__ int32_t dstart[kRadix];  // first tile position of each digit (digit order)
+    __shared__ int32_t wtot[kWarps];
+    __shared__ int2 stage[kTile];
     const int64_t count = count_of(d_count, n_cap);
     if (int64_t(blockIdx.x) * kTile >= count) return;  // nothing of this tile to place
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wcnt[0][0])[i] = 0;
@@ -126,23 +134,40 @@ __global__ void __launch_bounds__(kThreads)
         lrank[r] = pre + __popc(peers & lanemask_lt());
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += kThreads) {
-        int32_t run = 0;
+    // per digit (one per thread): counts of the warps -> exclusive offsets across warps, and the
+    // digit's total; then the digits' totals -> exclusive offsets across digits (block scan)
+    const int d = threadIdx.x;  // kThreads == kRadix
+    int32_t run = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            int32_t t = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += t;
-        }
-        gbase[d] = goff[int64_t(d) * nblocks + blockIdx.x];
+    for (int w = 0; w < kWarps; ++w) {
+        const int32_t t = wcnt[w][d];
+        wcnt[w][d] = run;
+        run += t;
     }
+    gbase[d] = goff[int64_t(d) * nblocks + blockIdx.x];
+    int32_t inc = run;  // inclusive scan of the digits' totals: warp scan, then the warps' sums
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const int32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == kWarp - 1) wtot[warp] = inc;
+    __syncthreads();
+    int32_t wofs = 0;
+    for (int w = 0; w < warp; ++w) wofs += wtot[w];
+    dstart[d] = wofs + inc - run;
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        if (dig[r] >= 0) {
-            int32_t dest = gbase[dig[r]] + wcnt[warp][dig[r]] + lrank[r];
-            kv_out[dest] = make_int2(key[r], val[r]);
-        }
+    for (int r = 0; r < kRounds; ++r)
+        if (dig[r] >= 0) stage[dstart[dig[r]] + wcnt[warp][dig[r]] + lrank[r]] = make_int2(key[r], val[r]);
+    __syncthreads();
+    int32_t placed = 0;  // elements of the tile with a valid key
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) placed += wtot[w];
+    for (int i = threadIdx.x; i < placed; i += kThreads) {
+        const int2 x = stage[i];
+        const int dd = (x.x >> shift) & (kRadix - 1);
+        kv_out[gbase[dd] + (i - dstart[dd])] = x;
     }
 }
 
