@@ -274,7 +274,7 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  *                           sublist) take one in 4 up to 2^15 elements, one in
  *                           8 up to 2^20, one in 16 up to 2^22, or this value
  *                           where it is denser
- *   ETL_TUNE_RANK_K_LOG2    density at the upper ranking levels, [1, 8] (4)
+ *   ETL_TUNE_RANK_K_LOG2    density at the upper ranking levels, [1, 8] (3)
  *   ETL_TUNE_RANK_BLOCK     threads per block of the walk kernels, one of
  *                           64, 128, 256, 512, 1024 (128)
  *   ETL_TUNE_RANK_BLOCKS_PER_SM  resident walk blocks per SM, block * value

@@ -179,7 +179,7 @@ struct RankResult {
 
 struct RankParams {
     int k0_log2 = 5;     // level-0 splitter density: one in 2^k0_log2 elements
-    int k_log2 = 4;      // density at the upper levels
+    int k_log2 = 3;      // density at the upper levels (1 in 8: 1-4% faster than 1 in 16 on trees of 2^15 .. 2^22)
     int block = 128;     // threads per block of the walk kernels
     int blocks_per_sm = 4;  // 512 walkers per SM: more of them measured slower (DRAM contention)
 };
