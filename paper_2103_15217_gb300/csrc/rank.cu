@@ -593,18 +593,18 @@ etl_status static_scratch(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ETL_ECUDA;
     std::lock_guard<std::mutex> g(g_static_mu);
+    // without the driver's context ids (entry points not found) the address is cached per device only
     unsigned long long id = 0;
     const bool have_id = current_context_id(&id);
-    if (!g_static_addr[dev] || !have_id || g_static_ctx[dev] != id) {
+    if (!g_static_addr[dev] || (have_id && g_static_ctx[dev] != id)) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_rank_scratch) != cudaSuccess || !p) return ETL_ECUDA;
         if (cudaFuncSetAttribute(k_pointer_jump, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kPjCap * 4) !=
             cudaSuccess)
             return ETL_ECUDA;
         // the look-up made the device's primary context current if it was not yet
-        if (!current_context_id(&id)) return ETL_ECUDA;
+        g_static_ctx[dev] = current_context_id(&id) ? id : 0;
         g_static_addr[dev] = p;
-        g_static_ctx[dev] = id;
     }
     *out = g_static_addr[dev];
     return ETL_OK;
