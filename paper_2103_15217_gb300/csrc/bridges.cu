@@ -221,7 +221,10 @@ __global__ void k_forest_succ(const int2 *__restrict__ B, const int32_t *__restr
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cap; i += int64_t(gridDim.x) * blockDim.x) {
         if (i < len) {
             const int2 bx = B[i];
-            const int32_t nb = (i + 1 < off[bx.y + 1]) ? B[i + 1].x : B[off[bx.y]].x;
+            // the group of tail bx.y continues at i + 1 iff that entry has the same tail; only the last
+            // entry of a group reads the group's start
+            const int2 nx = i + 1 < len ? B[i + 1] : make_int2(-1, -1);
+            const int32_t nb = nx.y == bx.y ? nx.x : B[off[bx.y]].x;
             succ[bx.x ^ 1] = nb;
         } else {
             succ[i] = ETL_END;

@@ -103,7 +103,9 @@ __global__ void k_count_children(const int32_t *__restrict__ parent, int32_t n, 
     }
 }
 
-// kv[t] = (parent, child), grouped by parent with children ascending
+// kv[t] = (parent, child), grouped by parent with children ascending. Child c at position t has a
+// next sibling iff position t + 1 holds the same parent (the groups are contiguous), which the
+// coalesced read of kv[t + 1] shows without a gather of the parent's group end.
 __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restrict__ coff, int32_t n,
                             int32_t *__restrict__ succ) {
     const int32_t kept = coff[n];  // number of (parent, child) pairs
@@ -115,7 +117,11 @@ __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restri
             const int2 pc = kv[t];
             const int32_t c = pc.y, p = pc.x;
             if (c >= 0 && c < n && p >= 0 && p < n) {
-                const int32_t sib = (t + 1 < coff[p + 1]) ? kv[t + 1].y : -1;
+                int32_t sib = -1;
+                if (t + 1 < kept) {
+                    const int2 nx = kv[t + 1];
+                    if (nx.x == p) sib = nx.y;
+                }
                 succ[2 * c + 1] = sib >= 0 ? 2 * sib : 2 * p + 1;  // leave c -> enter next sibling, or leave p
             }
         }
