@@ -7,8 +7,9 @@ result compared with the CPU oracle (bit-exact: all of it is integer work).
   m = 4n, small- and large-diameter alternating -- the inputs the benchmark
   times. They run through lca_preprocess_batch / lca_query_batch and
   find_bridges_batch, first eagerly and then replayed from one captured CUDA
-  graph with the tree batch and the graph batch on two streams, as the
-  benchmark launches them. At this scale the chained tour of all trees is a
+  graph with the tree batch and the graph batch on two parallel streams (the
+  benchmark runs them one after the other on one stream; the forked capture
+  also checks that the two batches share no scratch). At this scale the chained tour of all trees is a
   list far larger than L2, so the walk runs with the launch shape of large
   lists, and the connectivity pass spreads its edge chunks over 2048 graphs.
 * Served: 256 resident trees with n log-uniform in [2^10, 2^22] and the
