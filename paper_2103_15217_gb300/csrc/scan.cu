@@ -157,13 +157,13 @@ etl_status scan_impl(const T *in, int32_t *out, int64_t n, const int32_t *d_n, W
     int32_t *pscan = ws.get<int32_t>(nb + 1);
     if (!ws.ok()) return ETL_ENOMEM;
     k_reduce<T><<<unsigned(nb), kThreads, 0, s>>>(in, n, d_n, partial);
-        note_launch();
+    note_launch();
     etl_status st = last_launch();
     if (st) return st;
     st = scan_impl<int32_t>(partial, pscan, nb, nullptr, ws);
     if (st) return st;
     k_scan_tile<T><<<unsigned(nb), kThreads, 0, s>>>(in, out, n, d_n, pscan, nb);
-        note_launch();
+    note_launch();
     return last_launch();
 }
 
