@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kHookChunk)
     for (int64_t c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const int64_t e = hook_chunk(c, nsuper, spread) * kHookChunk + threadIdx.x;
         if (e >= m) continue;
-        int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        int32_t a = __ldcs(edges + 2 * e), b = __ldcs(edges + 2 * e + 1);
         uint8_t tree = 0;
         if (skip && skip[e]) {
             // left out
@@ -305,8 +305,8 @@ __global__ void k_nontree_minmax(const int32_t *__restrict__ edges, int64_t m, i
                                  const uint8_t *__restrict__ is_tree, const int32_t *__restrict__ tin,
                                  int32_t *__restrict__ nlo, int32_t *__restrict__ nhi) {
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
-        if (is_tree[e]) continue;
-        const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        if (__ldcs(is_tree + e)) continue;
+        const int32_t a = __ldcs(edges + 2 * e), b = __ldcs(edges + 2 * e + 1);
         if (a < 0 || a >= n || b < 0 || b >= n || a == b) continue;
         const int32_t ta = __ldg(tin + a), tb = __ldg(tin + b);
         // nlo(x) and nhi(x) start at tin(x): of the four updates only the one lowering the later

@@ -80,7 +80,7 @@ __global__ void k_count_children(const int32_t *__restrict__ parent, int32_t n, 
             gparent[v] = -2;
             continue;
         }
-        const int32_t p = parent[v];
+        const int32_t p = __ldcs(parent + v);
         int32_t inst = 0, base = 0, size = n;
         if (BATCH) {
             inst = inst_of[v];
@@ -111,7 +111,7 @@ __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restri
     const int32_t kept = coff[n];  // number of (parent, child) pairs
     for (int64_t t = gtid(); t < n; t += gstride()) {
         const int32_t v = int32_t(t);
-        const int32_t b = coff[v], e = coff[v + 1];
+        const int32_t b = __ldcs(coff + v), e = __ldcs(coff + v + 1);
         succ[2 * v] = (b < e) ? 2 * kv[b].y : 2 * v + 1;  // enter v -> enter first child, or leave v
         if (t < kept) {                                    // position t of the grouped children
             const int2 pc = kv[t];
@@ -133,7 +133,7 @@ __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restri
 __global__ void k_contract_leaves(const int32_t *__restrict__ coff, const int32_t *__restrict__ par, int32_t n,
                                   int32_t *__restrict__ succ) {
     for (int64_t t = gtid(); t < n; t += gstride()) {
-        if (coff[t] != coff[t + 1] || par[t] < 0) continue;  // has children, or is a root
+        if (__ldcs(coff + t) != __ldcs(coff + t + 1) || __ldcs(par + t) < 0) continue;  // has children, or is a root
         const int32_t nx = succ[2 * t + 1];
         if (nx < 0) continue;                               // malformed: leave it to the validity checks
         succ[2 * t] = int32_t(uint32_t(nx) | 0x80000000u);
@@ -161,13 +161,13 @@ __global__ void k_node_stats(RankResult rr, const int32_t *__restrict__ succ, in
                              int32_t *__restrict__ status) {
     const uint4 *pk = reinterpret_cast<const uint4 *>(rr.packed);  // brackets 2v and 2v+1 side by side
     for (int64_t t = gtid(); t < n; t += gstride()) {
-        const bool leaf = succ[2 * t] < ETL_END;  // contracted: the closing bracket is ranked right after
+        const bool leaf = __ldcs(succ + 2 * t) < ETL_END;  // contracted: the closing bracket is ranked right after
         uint4 q;
         if (leaf) {
-            const uint2 a = rr.packed[2 * t];
+            const uint2 a = __ldcs(rr.packed + 2 * t);
             q = make_uint4(a.x, a.y, a.x, 0u);
         } else {
-            q = pk[t];
+            q = __ldcs(pk + t);
         }
         if (q.x >= rr.rcap || q.z >= rr.rcap) {  // not on the list from the root: malformed input
             set_status(status, ETL_EBADTREE);
@@ -177,9 +177,9 @@ __global__ void k_node_stats(RankResult rr, const int32_t *__restrict__ succ, in
         const uint2 in = make_uint2(q.x, q.y), out = make_uint2(q.z, q.w);
         const int32_t r0 = rank_of(rr, in), r1 = leaf ? r0 + 1 : rank_of(rr, out);
         const int32_t p = evens_before(rr, in);
-        pre[t] = p;
-        depth[t] = 2 * p - r0;
-        size[t] = (r1 - r0 + 1) >> 1;
+        __stcs(pre + t, p);
+        __stcs(depth + t, 2 * p - r0);
+        __stcs(size + t, (r1 - r0 + 1) >> 1);
         if (p >= 0 && p < n) order[p] = int32_t(t);
     }
 }
@@ -197,14 +197,14 @@ __global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *
 #pragma unroll
         for (int j = 0; j < kGatherIlp; ++j) {
             const int64_t i = base + int64_t(j) * blockDim.x;
-            v[j] = i < n ? order[i] : -1;
+            v[j] = i < n ? __ldcs(order + i) : -1;
         }
 #pragma unroll
         for (int j = 0; j < kGatherIlp; ++j) p[j] = (v[j] >= 0 && v[j] < n) ? __ldg(parent + v[j]) : -1;
 #pragma unroll
         for (int j = 0; j < kGatherIlp; ++j) {
             const int64_t i = base + int64_t(j) * blockDim.x;
-            if (i < n) q0[i] = (p[j] >= 0 && p[j] < n) ? __ldg(pre + p[j]) : -1;
+            if (i < n) __stcs(q0 + i, (p[j] >= 0 && p[j] < n) ? __ldg(pre + p[j]) : -1);
         }
     }
 }
@@ -243,13 +243,13 @@ __global__ void k_node_rec(const int32_t *__restrict__ pre, const int32_t *__res
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             const int64_t w = base + int64_t(j) * blockDim.x;
-            p[j] = w < n ? pre[w] : -1;
+            p[j] = w < n ? __ldcs(pre + w) : -1;
             e[j] = (p[j] >= 0 && p[j] < n) ? __ldg(pmsm + p[j]) : make_int2(INT_MAX, INT_MAX);  // bad tree: flagged
         }
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             const int64_t w = base + int64_t(j) * blockDim.x;
-            if (w < n) nrec[w] = make_int4(p[j], e[j].x, e[j].y, size[w]);
+            if (w < n) __stcs(nrec + w, make_int4(p[j], e[j].x, e[j].y, __ldcs(size + w)));
         }
     }
 }
