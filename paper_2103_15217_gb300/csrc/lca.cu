@@ -16,6 +16,9 @@
 //      cyclic list cut at the root: the root's two brackets start and end
 //      its tour. k_link_roots chains the tours of a batch, root i's closing
 //      bracket -> root i+1's opening bracket, so one list covers all trees.
+//      The two halves are written apart (the closing brackets' successors at
+//      random places into an array of n entries that L2 holds) and
+//      interleaved by k_tour_assemble, which also contracts the leaves.
 //   4. list ranking (rank.cu), counting opening brackets on the way.
 //   5. k_node_stats: preorder = opening brackets before 2v; depth =
 //      2*pre - rank(2v) (opening minus closing brackets before it, the +1/-1
@@ -105,15 +108,19 @@ __global__ void k_count_children(const int32_t *__restrict__ parent, int32_t n, 
 
 // kv[t] = (parent, child), grouped by parent with children ascending. Child c at position t has a
 // next sibling iff position t + 1 holds the same parent (the groups are contiguous), which the
-// coalesced read of kv[t + 1] shows without a gather of the parent's group end.
+// coalesced read of kv[t + 1] shows without a gather of the parent's group end. The successors of
+// the opening brackets go to so[v] (coalesced), those of the closing brackets to sc[c]: written at
+// random places, they stay within n entries, which L2 holds while they are written (in place, at
+// succ[2c + 1], they spread over twice the memory and the kernel ran 2.2x slower);
+// k_tour_assemble interleaves the two.
 __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restrict__ coff, int32_t n,
-                            int32_t *__restrict__ succ) {
+                            int32_t *__restrict__ so, int32_t *__restrict__ sc) {
     const int32_t kept = coff[n];  // number of (parent, child) pairs
     for (int64_t t = gtid(); t < n; t += gstride()) {
         const int32_t v = int32_t(t);
         const int32_t b = __ldcs(coff + v), e = __ldcs(coff + v + 1);
-        succ[2 * v] = (b < e) ? 2 * kv[b].y : 2 * v + 1;  // enter v -> enter first child, or leave v
-        if (t < kept) {                                    // position t of the grouped children
+        __stcs(so + v, (b < e) ? 2 * kv[b].y : 2 * v + 1);  // enter v -> enter first child, or leave v
+        if (t < kept) {                                      // position t of the grouped children
             const int2 pc = kv[t];
             const int32_t c = pc.y, p = pc.x;
             if (c >= 0 && c < n && p >= 0 && p < n) {
@@ -122,29 +129,31 @@ __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restri
                     const int2 nx = kv[t + 1];
                     if (nx.x == p) sib = nx.y;
                 }
-                succ[2 * c + 1] = sib >= 0 ? 2 * sib : 2 * p + 1;  // leave c -> enter next sibling, or leave p
+                sc[c] = sib >= 0 ? 2 * sib : 2 * p + 1;  // leave c -> enter next sibling, or leave p
             }
         }
     }
 }
 
-// A leaf v's brackets are adjacent in the tour: 2v jumps straight to the successor of 2v+1 with
-// weight 2 (top bit set), and 2v+1 leaves the list. Roots are never contracted.
-__global__ void k_contract_leaves(const int32_t *__restrict__ coff, const int32_t *__restrict__ par, int32_t n,
-                                  int32_t *__restrict__ succ) {
+// succ[2v] = so[v], succ[2v + 1] = sc[v], one 8-byte store per node. A leaf v's brackets are
+// adjacent in the tour: 2v jumps straight to the successor of 2v+1 with weight 2 (top bit set), and
+// 2v+1 leaves the list. Roots are never contracted.
+__global__ void k_tour_assemble(const int32_t *__restrict__ coff, const int32_t *__restrict__ par,
+                                const int32_t *__restrict__ so, const int32_t *__restrict__ sc, int32_t n,
+                                int32_t *__restrict__ succ) {
+    int2 *pair = reinterpret_cast<int2 *>(succ);
     for (int64_t t = gtid(); t < n; t += gstride()) {
-        if (__ldcs(coff + t) != __ldcs(coff + t + 1) || __ldcs(par + t) < 0) continue;  // has children, or is a root
-        const int32_t nx = succ[2 * t + 1];
-        if (nx < 0) continue;                               // malformed: leave it to the validity checks
-        succ[2 * t] = int32_t(uint32_t(nx) | 0x80000000u);
-        succ[2 * t + 1] = ETL_END;
+        const bool leaf = __ldcs(coff + t) == __ldcs(coff + t + 1) && __ldcs(par + t) >= 0;  // no children, no root
+        const int32_t a = __ldcs(so + t), c = __ldcs(sc + t);
+        // a malformed close successor (c < 0) stays uncontracted: the validity checks see it
+        pair[t] = (leaf && c >= 0) ? make_int2(int32_t(uint32_t(c) | 0x80000000u), ETL_END) : make_int2(a, c);
     }
 }
 
 // exactly one root per instance; leave root i -> enter root i+1 (or end of the list after the last
 // tree); the list starts at the first root's opening bracket
 __global__ void k_link_roots(const int32_t *__restrict__ root_cnt, const int32_t *__restrict__ root_of, int32_t k,
-                             int32_t n, int32_t *__restrict__ succ, int32_t *__restrict__ head,
+                             int32_t n, int32_t *__restrict__ sc, int32_t *__restrict__ head,
                              int32_t *__restrict__ status) {
     if (gtid() == 0) *head = 2 * root_of[0];
     for (int64_t i = gtid(); i < k; i += gstride()) {
@@ -152,7 +161,7 @@ __global__ void k_link_roots(const int32_t *__restrict__ root_cnt, const int32_t
         const int32_t r = root_of[i];
         if (r < 0 || r >= n) continue;
         const int32_t nr = (i + 1 < k) ? root_of[i + 1] : -1;
-        succ[2 * r + 1] = (nr >= 0 && nr < n) ? 2 * nr : ETL_END;
+        sc[r] = (nr >= 0 && nr < n) ? 2 * nr : ETL_END;
     }
 }
 
@@ -414,6 +423,7 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
         int32_t *coff = ws.get<int32_t>(int64_t(n) + 1);
         int32_t *misc = ws.get<int32_t>(4);  // [0] list head, [1] offsets invalid
         int32_t *succ = ws.get<int32_t>(2 * int64_t(n));
+        int32_t *sc = ws.get<int32_t>(n);  // successors of the closing brackets; those of the opening ones reuse cnt
         int32_t *root_cnt = ws.get<int32_t>(k), *root_of = ws.get<int32_t>(k);
         int32_t *inst_of = batch ? ws.get<int32_t>(n) : nullptr;
         int32_t *gparent = batch ? ws.get<int32_t>(n) : nullptr;
@@ -445,11 +455,12 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
         if (!st) st = radix_sort_pairs(par, nullptr, nullptr, n, ceil_log2(uint64_t(n)), n, ws, &sr);
         if (!st) {
             PhaseTimer pt("lca.succ", s);
-            k_tour_succ<<<grid_for(n, 256), 256, 0, s>>>(sr.kv, coff, n, succ);
+            int32_t *so = cnt;  // the child counts are no longer needed once the offsets are scanned
+            k_tour_succ<<<grid_for(n, 256), 256, 0, s>>>(sr.kv, coff, n, so, sc);
             note_launch();
-            k_link_roots<<<grid_for(k, 256), 256, 0, s>>>(root_cnt, root_of, k, n, succ, misc, h->status);
+            k_link_roots<<<grid_for(k, 256), 256, 0, s>>>(root_cnt, root_of, k, n, sc, misc, h->status);
             note_launch();
-            k_contract_leaves<<<grid_for(n, 256), 256, 0, s>>>(coff, par, n, succ);
+            k_tour_assemble<<<grid_for(n, 256), 256, 0, s>>>(coff, par, so, sc, n, succ);
             note_launch();
             st = last_launch();
         }
