@@ -307,6 +307,12 @@ etl_status find_bridges(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
  *   ETL_TUNE_SORT_BALLOT    1: the radix scatter finds the lanes holding the
  *                           same digit with eight warp ballots; 0: with
  *                           __match_any_sync (1)
+ *   ETL_TUNE_PDL            1: the library's kernels are launched with
+ *                           programmatic dependent launch, so each one is
+ *                           scheduled while the kernel before it on the
+ *                           stream finishes, and waits for its results on the
+ *                           device (CUDA-graph captures keep the overlap); 0:
+ *                           plain stream order (1)
  * Unknown keys or out-of-range values return ETL_EINVAL.
  */
 enum {
@@ -321,7 +327,8 @@ enum {
     ETL_TUNE_SORT_ROUNDS = 9,
     ETL_TUNE_CC_DOUBLING = 10,
     ETL_TUNE_CC_GIANT = 11,
-    ETL_TUNE_SORT_BALLOT = 12
+    ETL_TUNE_SORT_BALLOT = 12,
+    ETL_TUNE_PDL = 13
 };
 etl_status etl_tune_set(int32_t key, int32_t value);
 etl_status etl_tune_get(int32_t key, int32_t *value);

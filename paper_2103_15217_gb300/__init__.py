@@ -37,7 +37,7 @@ WS_KINDS = {"list_rank": 1, "lca_preprocess": 2, "lca_query": 3, "find_bridges":
 TUNE_KEYS = {"rank_k0_log2": 1, "rank_k_log2": 2, "rank_block": 3, "rank_blocks_per_sm": 4,
              "rmq_levels_per_pass": 5, "rmq_block": 6, "cc_first_slice": 7,
              "rmq_blocked": 8, "sort_rounds": 9, "cc_doubling": 10,
-             "cc_giant": 11, "sort_ballot": 12}
+             "cc_giant": 11, "sort_ballot": 12, "pdl": 13}
 
 _lock = threading.Lock()
 _lib = None

@@ -6,6 +6,11 @@
 
 namespace etl {
 
+bool &pdl_enabled() {
+    static bool on = true;
+    return on;
+}
+
 int num_sms() {
     static std::mutex mu;
     static int cached[64] = {0};
@@ -199,6 +204,10 @@ extern "C" etl_status etl_tune_set(int32_t key, int32_t value) {
             if (value != 0 && value != 1) return ETL_EINVAL;
             sort_params().ballot = value != 0;
             return ETL_OK;
+        case ETL_TUNE_PDL:
+            if (value != 0 && value != 1) return ETL_EINVAL;
+            pdl_enabled() = value != 0;
+            return ETL_OK;
         default:
             return ETL_EINVAL;
     }
@@ -220,6 +229,7 @@ extern "C" etl_status etl_tune_get(int32_t key, int32_t *value) {
         case ETL_TUNE_CC_DOUBLING: *value = cc_params().doubling ? 1 : 0; return ETL_OK;
         case ETL_TUNE_CC_GIANT: *value = cc_params().giant ? 1 : 0; return ETL_OK;
         case ETL_TUNE_SORT_BALLOT: *value = sort_params().ballot ? 1 : 0; return ETL_OK;
+        case ETL_TUNE_PDL: *value = pdl_enabled() ? 1 : 0; return ETL_OK;
         default: return ETL_EINVAL;
     }
 }

@@ -38,6 +38,7 @@ namespace {
 constexpr int64_t kFindCap = int64_t(1) << 26;  // bound on pointer-chasing steps of one edge
 
 __global__ void k_init(int32_t n, int32_t *__restrict__ par, int32_t *__restrict__ deg, int32_t *__restrict__ tin) {
+    pdl_prologue();
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
         par[v] = int32_t(v);
         deg[v] = 0;
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(kHookChunk)
     k_hook(const int32_t *__restrict__ edges, int64_t m, int64_t c0, int64_t c1, bool spread, int32_t n,
            int32_t *__restrict__ par, uint8_t *__restrict__ is_tree, const uint8_t *__restrict__ skip,
            const int32_t *__restrict__ d_giant, int32_t *__restrict__ status) {
+    pdl_prologue();
     const int32_t giant = d_giant ? *d_giant : -1;
     const int64_t nsuper = ((m + kHookChunk - 1) / kHookChunk + kHookSuper - 1) / kHookSuper;
     for (int64_t c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(kHookChunk)
 }
 
 __global__ void k_compress(int32_t n, int32_t *__restrict__ par, int32_t *__restrict__ status) {
+    pdl_prologue();
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
         int64_t budget = kFindCap;
         const int32_t r = find_root(par, int32_t(v), budget);
@@ -149,6 +152,7 @@ constexpr int kGiantSample = 1024;
 
 __global__ void __launch_bounds__(kGiantSample) k_giant(const int32_t *__restrict__ par, int32_t n,
                                                          int32_t *__restrict__ giant) {
+    pdl_prologue();
     constexpr int kSlots = 2 * kGiantSample;  // open-addressing table of (root, count)
     __shared__ int32_t key[kSlots], cnt[kSlots];
     __shared__ unsigned long long best;
@@ -183,6 +187,7 @@ __global__ void __launch_bounds__(kGiantSample) k_giant(const int32_t *__restric
 __global__ void k_forest_edges(const int32_t *__restrict__ edges, int64_t m, const uint8_t *__restrict__ is_tree,
                                const int32_t *__restrict__ tpos, int32_t *__restrict__ tuv,
                                int32_t *__restrict__ tedge, int32_t *__restrict__ n_arcs) {
+    pdl_prologue();
     if (blockIdx.x == 0 && threadIdx.x == 0) *n_arcs = 2 * tpos[m];
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
         if (is_tree[e]) {
@@ -197,6 +202,7 @@ __global__ void k_forest_edges(const int32_t *__restrict__ edges, int64_t m, con
 // half-edges per tail vertex
 __global__ void k_arc_count(const int32_t *__restrict__ tuv, const int32_t *__restrict__ d_len,
                             int32_t *__restrict__ deg) {
+    pdl_prologue();
     const int64_t len = *d_len;
     for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < len; a += int64_t(gridDim.x) * blockDim.x)
         atomicAdd(&deg[tuv[a]], 1);
@@ -205,6 +211,7 @@ __global__ void k_arc_count(const int32_t *__restrict__ tuv, const int32_t *__re
 // B[i] = (half-edge, tail) grouped by tail: off[x] .. off[x+1]-1 are the half-edges leaving x
 __global__ void k_arc_scatter(const int32_t *__restrict__ tuv, const int32_t *__restrict__ d_len,
                               const int32_t *__restrict__ off, int32_t *__restrict__ deg, int2 *__restrict__ B) {
+    pdl_prologue();
     const int64_t len = *d_len;
     for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < len; a += int64_t(gridDim.x) * blockDim.x) {
         const int32_t x = tuv[a];
@@ -217,6 +224,7 @@ __global__ void k_arc_scatter(const int32_t *__restrict__ tuv, const int32_t *__
 // slots beyond the forest (and the virtual head, set later) are inert
 __global__ void k_forest_succ(const int2 *__restrict__ B, const int32_t *__restrict__ d_len, int64_t cap,
                               const int32_t *__restrict__ off, int32_t *__restrict__ succ) {
+    pdl_prologue();
     const int64_t len = *d_len;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cap; i += int64_t(gridDim.x) * blockDim.x) {
         if (i < len) {
@@ -234,12 +242,14 @@ __global__ void k_forest_succ(const int2 *__restrict__ B, const int32_t *__restr
 
 __global__ void k_root_flags(int32_t n, const int32_t *__restrict__ par, const int32_t *__restrict__ off,
                              uint8_t *__restrict__ flag) {
+    pdl_prologue();
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
         flag[v] = (par[v] == v && off[v + 1] > off[v]) ? 1 : 0;
 }
 
 __global__ void k_root_list(int32_t n, const uint8_t *__restrict__ flag, const int32_t *__restrict__ rpos,
                             int32_t *__restrict__ roots) {
+    pdl_prologue();
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
         if (flag[v]) roots[rpos[v]] = int32_t(v);
 }
@@ -249,6 +259,7 @@ __global__ void k_root_list(int32_t n, const uint8_t *__restrict__ flag, const i
 __global__ void k_chain(int32_t n, const int32_t *__restrict__ rpos, const int32_t *__restrict__ roots,
                         const int2 *__restrict__ B, const int32_t *__restrict__ off, int32_t vhead,
                         int32_t *__restrict__ succ) {
+    pdl_prologue();
     const int32_t c = rpos[n];
     if (blockIdx.x == 0 && threadIdx.x == 0) succ[vhead] = c > 0 ? B[off[roots[0]]].x : ETL_END;
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < c; k += int64_t(gridDim.x) * blockDim.x) {
@@ -262,6 +273,7 @@ __global__ void k_chain(int32_t n, const int32_t *__restrict__ rpos, const int32
 __global__ void k_forest_tin(RankResult rr, const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ tuv,
                              int32_t *__restrict__ tin, int32_t *__restrict__ child, int32_t *__restrict__ etin,
                              int32_t *__restrict__ etout) {
+    pdl_prologue();
     const int64_t T = *d_arcs / 2;
     const uint4 *pk = reinterpret_cast<const uint4 *>(rr.packed);
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
@@ -284,6 +296,7 @@ __global__ void k_forest_tin(RankResult rr, const int32_t *__restrict__ d_arcs, 
 __global__ void k_root_tin(int32_t n, const int32_t *__restrict__ rpos, const int32_t *__restrict__ roots,
                            const int2 *__restrict__ B, const int32_t *__restrict__ off, RankResult rr,
                            int32_t *__restrict__ tin) {
+    pdl_prologue();
     const int32_t c = rpos[n];
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < c; k += int64_t(gridDim.x) * blockDim.x) {
         const int32_t r = roots[k];
@@ -294,6 +307,7 @@ __global__ void k_root_tin(int32_t n, const int32_t *__restrict__ rpos, const in
 
 __global__ void k_nlo_init(int32_t n, const int32_t *__restrict__ tin, int32_t *__restrict__ nlo,
                            int32_t *__restrict__ nhi) {
+    pdl_prologue();
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
         const int32_t x = tin[v];
         nlo[v] = x;
@@ -304,6 +318,7 @@ __global__ void k_nlo_init(int32_t n, const int32_t *__restrict__ tin, int32_t *
 __global__ void k_nontree_minmax(const int32_t *__restrict__ edges, int64_t m, int32_t n,
                                  const uint8_t *__restrict__ is_tree, const int32_t *__restrict__ tin,
                                  int32_t *__restrict__ nlo, int32_t *__restrict__ nhi) {
+    pdl_prologue();
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
         if (__ldcs(is_tree + e)) continue;
         const int32_t a = __ldcs(edges + 2 * e), b = __ldcs(edges + 2 * e + 1);
@@ -327,6 +342,7 @@ __global__ void k_place(const int32_t *__restrict__ d_arcs, const int32_t *__res
                         const int32_t *__restrict__ etin, const int32_t *__restrict__ etout,
                         const int32_t *__restrict__ nlo, const int32_t *__restrict__ nhi, int64_t P,
                         int32_t *__restrict__ L, int32_t *__restrict__ H) {
+    pdl_prologue();
     const int64_t T = *d_arcs / 2;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         L[0] = INT_MAX;
@@ -347,6 +363,7 @@ __global__ void k_place2(const int32_t *__restrict__ d_arcs, const int32_t *__re
                          const int32_t *__restrict__ etin, const int32_t *__restrict__ etout,
                          const int32_t *__restrict__ nlo, const int32_t *__restrict__ nhi, int64_t P,
                          int2 *__restrict__ LH) {
+    pdl_prologue();
     const int64_t T = *d_arcs / 2;
     const int2 id = make_int2(INT_MAX, INT_MIN);
     if (blockIdx.x == 0 && threadIdx.x == 0) LH[0] = id;
@@ -361,6 +378,7 @@ __global__ void k_place2(const int32_t *__restrict__ d_arcs, const int32_t *__re
 __global__ void k_bridge_test2(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ etin,
                                const int32_t *__restrict__ etout, BlockedView<OpMinMax> lh, int64_t P,
                                uint8_t *__restrict__ tflag) {
+    pdl_prologue();
     const int64_t T = *d_arcs / 2;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
         const int32_t a = etin[t], b = etout[t];
@@ -376,6 +394,7 @@ __global__ void k_bridge_test2(const int32_t *__restrict__ d_arcs, const int32_t
 __global__ void k_bridge_test(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ etin,
                               const int32_t *__restrict__ etout, const int32_t *__restrict__ Lt,
                               const int32_t *__restrict__ Ht, int64_t P, int64_t ld, uint8_t *__restrict__ tflag) {
+    pdl_prologue();
     const int64_t T = *d_arcs / 2;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
         const int32_t a = etin[t], b = etout[t];
@@ -392,6 +411,7 @@ __global__ void k_bridge_test(const int32_t *__restrict__ d_arcs, const int32_t 
 __global__ void k_finalize(int64_t m, const uint8_t *__restrict__ is_tree, const int32_t *__restrict__ tpos,
                            const uint8_t *__restrict__ tflag, const int32_t *__restrict__ status,
                            uint8_t *__restrict__ is_bridge) {
+    pdl_prologue();
     const bool bad = *status != 0;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x)
         is_bridge[e] = (!bad && is_tree[e]) ? tflag[tpos[e]] : 0;
@@ -425,6 +445,7 @@ namespace {
 
 __global__ void k_tour_pm(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ etin,
                           const int32_t *__restrict__ etout, int64_t P, int32_t *__restrict__ val) {
+    pdl_prologue();
     const int64_t T = *d_arcs / 2;
     if (blockIdx.x == 0 && threadIdx.x == 0) val[0] = 0;  // the virtual head
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
@@ -439,6 +460,7 @@ __global__ void k_tree_records(int32_t n, const int32_t *__restrict__ d_arcs, co
                                const int32_t *__restrict__ child, const int32_t *__restrict__ etin,
                                const int32_t *__restrict__ excl, int64_t P, int2 *__restrict__ trec,
                                uint8_t *__restrict__ mark) {
+    pdl_prologue();
     const int64_t T = *d_arcs / 2;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x) {
         const int32_t c = child[t], a = etin[t];
@@ -450,12 +472,14 @@ __global__ void k_tree_records(int32_t n, const int32_t *__restrict__ d_arcs, co
 }
 
 __global__ void k_tree_records_init(int32_t n, int2 *__restrict__ trec) {
+    pdl_prologue();
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
         trec[v] = make_int2(-1, 0);  // roots and isolated vertices
 }
 
 __global__ void k_ck_mark(const int32_t *__restrict__ edges, int64_t m, int32_t n, const uint8_t *__restrict__ is_tree,
                           const int2 *__restrict__ trec, uint8_t *__restrict__ mark, int32_t *__restrict__ status) {
+    pdl_prologue();
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
         if (is_tree[e]) continue;
         int32_t a = edges[2 * e], b = edges[2 * e + 1];
@@ -484,6 +508,7 @@ __global__ void k_ck_mark(const int32_t *__restrict__ edges, int64_t m, int32_t 
 
 __global__ void k_ck_flags(const int32_t *__restrict__ d_arcs, const int32_t *__restrict__ child,
                            const uint8_t *__restrict__ mark, uint8_t *__restrict__ tflag) {
+    pdl_prologue();
     const int64_t T = *d_arcs / 2;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < T; t += int64_t(gridDim.x) * blockDim.x)
         tflag[t] = mark[child[t]] ? 0 : 1;
@@ -501,20 +526,20 @@ etl_status hybrid_marking(const int32_t *edges, int64_t m, int32_t n, const uint
     const int gn = grid_for(n, 256);
     {
         PhaseTimer pt("hybrid.levels", s);
-        k_tour_pm<<<gn, 256, 0, s>>>(n_arcs, etin, etout, P, val);
+        launch(k_tour_pm, gn, 256, 0, s, n_arcs, etin, etout, P, val);
         note_launch();
     }
     etl_status rc = last_launch();
     if (!rc) rc = scan_exclusive_i32(val, excl, P, ws);
     if (rc) return rc;
     PhaseTimer pt("hybrid.mark", s);
-    k_tree_records_init<<<gn, 256, 0, s>>>(n, trec);
+    launch(k_tree_records_init, gn, 256, 0, s, n, trec);
     note_launch();
-    k_tree_records<<<gn, 256, 0, s>>>(n, n_arcs, tuv, child, etin, excl, P, trec, mark);
+    launch(k_tree_records, gn, 256, 0, s, n, n_arcs, tuv, child, etin, excl, P, trec, mark);
     note_launch();
-    k_ck_mark<<<grid_for(m, 256), 256, 0, s>>>(edges, m, n, is_tree, trec, mark, st);
+    launch(k_ck_mark, grid_for(m, 256), 256, 0, s, edges, m, n, is_tree, trec, mark, st);
     note_launch();
-    k_ck_flags<<<gn, 256, 0, s>>>(n_arcs, child, mark, tflag);
+    launch(k_ck_flags, gn, 256, 0, s, n_arcs, child, mark, tflag);
     note_launch();
     return last_launch();
 }
@@ -549,7 +574,7 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     const int gn = grid_for(n, 256), gm = grid_for(m, 256), gA = grid_for(N, 256);
     {
         PhaseTimer pt("br.init", s);
-        k_init<<<gn, 256, 0, s>>>(n, par, deg, tin);
+        launch(k_init, gn, 256, 0, s, n, par, deg, tin);
         note_launch();
     }
     {
@@ -565,15 +590,15 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
         for (int64_t c0 = 0; c0 < nchunks;) {
             const int64_t c1 = (C.doubling || c0 == 0) ? (c0 + w < nchunks ? c0 + w : nchunks) : nchunks;
             if (c0 > 0) {
-                k_compress<<<gn, 256, 0, s>>>(n, par, st);
+                launch(k_compress, gn, 256, 0, s, n, par, st);
                 note_launch();
                 if (C.giant) {
-                    k_giant<<<1, kGiantSample, 0, s>>>(par, n, giant);
+                    launch(k_giant, 1, kGiantSample, 0, s, par, n, giant);
                     note_launch();
                 }
             }
-            k_hook<<<grid_for((c1 - c0) * kHookChunk, kHookChunk), kHookChunk, 0, s>>>(
-                edges, m, c0, c1, spread, n, par, is_tree, nullptr, (c0 > 0 && C.giant) ? giant : nullptr, st);
+            launch(k_hook, grid_for((c1 - c0) * kHookChunk, kHookChunk), kHookChunk, 0, s, edges, m, c0, c1, spread, n,
+                   par, is_tree, nullptr, (c0 > 0 && C.giant) ? giant : nullptr, st);
             note_launch();
             c0 = c1;
             w *= 2;
@@ -581,40 +606,40 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     }
     {
         PhaseTimer pt("br.compress", s);
-        k_compress<<<gn, 256, 0, s>>>(n, par, st);
+        launch(k_compress, gn, 256, 0, s, n, par, st);
         note_launch();
     }
     rc = last_launch();
     if (!rc) rc = scan_exclusive_u8(is_tree, tpos, m, ws);
     if (!rc) {
         PhaseTimer pt("br.forest_edges", s);
-        k_forest_edges<<<gm, 256, 0, s>>>(edges, m, is_tree, tpos, tuv, tedge, n_arcs);
+        launch(k_forest_edges, gm, 256, 0, s, edges, m, is_tree, tpos, tuv, tedge, n_arcs);
         note_launch();
         rc = last_launch();
     }
     if (!rc) {
         PhaseTimer pt("br.group", s);
-        k_arc_count<<<gA, 256, 0, s>>>(tuv, n_arcs, deg);
+        launch(k_arc_count, gA, 256, 0, s, tuv, n_arcs, deg);
         note_launch();
         rc = last_launch();
     }
     if (!rc) rc = scan_exclusive_i32(deg, off, n, ws);
     if (!rc) {
         PhaseTimer pt("br.forest_succ", s);
-        k_arc_scatter<<<gA, 256, 0, s>>>(tuv, n_arcs, off, deg, B);
+        launch(k_arc_scatter, gA, 256, 0, s, tuv, n_arcs, off, deg, B);
         note_launch();
-        k_forest_succ<<<gA, 256, 0, s>>>(B, n_arcs, N, off, succ);
+        launch(k_forest_succ, gA, 256, 0, s, B, n_arcs, N, off, succ);
         note_launch();
-        k_root_flags<<<gn, 256, 0, s>>>(n, par, off, rflag);
+        launch(k_root_flags, gn, 256, 0, s, n, par, off, rflag);
         note_launch();
         rc = last_launch();
     }
     if (!rc) rc = scan_exclusive_u8(rflag, rpos, n, ws);
     if (!rc) {
         PhaseTimer pt("br.chain", s);
-        k_root_list<<<gn, 256, 0, s>>>(n, rflag, rpos, roots);
+        launch(k_root_list, gn, 256, 0, s, n, rflag, rpos, roots);
         note_launch();
-        k_chain<<<gn, 256, 0, s>>>(n, rpos, roots, B, off, int32_t(A), succ);
+        launch(k_chain, gn, 256, 0, s, n, rpos, roots, B, off, int32_t(A), succ);
         note_launch();
         rc = last_launch();
     }
@@ -624,16 +649,16 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     if (!rc) {
         const int gt = grid_for(n, 256);
         PhaseTimer pt("br.lowhigh_prep", s);
-        k_forest_tin<<<gt, 256, 0, s>>>(rr, n_arcs, tuv, tin, child, etin, etout);
+        launch(k_forest_tin, gt, 256, 0, s, rr, n_arcs, tuv, tin, child, etin, etout);
         note_launch();
-        k_root_tin<<<gn, 256, 0, s>>>(n, rpos, roots, B, off, rr, tin);
+        launch(k_root_tin, gn, 256, 0, s, n, rpos, roots, B, off, rr, tin);
         note_launch();
         rc = last_launch();
     }
     if (hybrid) {
         if (!rc) rc = hybrid_marking(edges, m, n, is_tree, tpos, tuv, n_arcs, child, etin, etout, P, tflag, st, ws);
         if (!rc) {
-            k_finalize<<<gm, 256, 0, s>>>(m, is_tree, tpos, tflag, st, is_bridge);
+            launch(k_finalize, gm, 256, 0, s, m, is_tree, tpos, tflag, st, is_bridge);
             note_launch();
             rc = last_launch();
         }
@@ -642,14 +667,14 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     if (!rc) {
         const int gt = grid_for(n, 256);
         PhaseTimer pt("br.lowhigh_prep", s);
-        k_nlo_init<<<gn, 256, 0, s>>>(n, tin, nlo, nhi);
+        launch(k_nlo_init, gn, 256, 0, s, n, tin, nlo, nhi);
         note_launch();
-        k_nontree_minmax<<<gm, 256, 0, s>>>(edges, m, n, is_tree, tin, nlo, nhi);
+        launch(k_nontree_minmax, gm, 256, 0, s, edges, m, n, is_tree, tin, nlo, nhi);
         note_launch();
         if (blocked)
-            k_place2<<<gt, 256, 0, s>>>(n_arcs, child, etin, etout, nlo, nhi, P, LH);
+            launch(k_place2, gt, 256, 0, s, n_arcs, child, etin, etout, nlo, nhi, P, LH);
         else
-            k_place<<<gt, 256, 0, s>>>(n_arcs, child, etin, etout, nlo, nhi, P, Lt, Ht);
+            launch(k_place, gt, 256, 0, s, n_arcs, child, etin, etout, nlo, nhi, P, Lt, Ht);
         note_launch();
         rc = last_launch();
     }
@@ -662,12 +687,12 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
     if (!rc) {
         PhaseTimer pt("br.test", s);
         if (blocked)
-            k_bridge_test2<<<grid_for(n, 256), 256, 0, s>>>(n_arcs, etin, etout, blocked_view<OpMinMax>(LH, bl), P,
-                                                           tflag);
+            launch(k_bridge_test2, grid_for(n, 256), 256, 0, s, n_arcs, etin, etout, blocked_view<OpMinMax>(LH, bl), P,
+                   tflag);
         else
-            k_bridge_test<<<grid_for(n, 256), 256, 0, s>>>(n_arcs, etin, etout, Lt, Ht, P, ld, tflag);
+            launch(k_bridge_test, grid_for(n, 256), 256, 0, s, n_arcs, etin, etout, Lt, Ht, P, ld, tflag);
         note_launch();
-        k_finalize<<<gm, 256, 0, s>>>(m, is_tree, tpos, tflag, st, is_bridge);
+        launch(k_finalize, gm, 256, 0, s, m, is_tree, tpos, tflag, st, is_bridge);
         note_launch();
         rc = last_launch();
     }
@@ -675,11 +700,13 @@ etl_status bridges_core(const int32_t *edges, int64_t m, int32_t n, uint8_t *is_
 }
 
 __global__ void k_iota(int32_t n, int32_t *__restrict__ x) {
+    pdl_prologue();
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
         x[v] = int32_t(v);
 }
 
 __global__ void k_labels_on_error(int32_t n, const int32_t *__restrict__ status, int32_t *__restrict__ label) {
+    pdl_prologue();
     if (*status == 0) return;
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
         label[v] = -1;
@@ -689,6 +716,7 @@ __global__ void k_labels_on_error(int32_t n, const int32_t *__restrict__ status,
 // joins node_off[i] + u and node_off[i] + v
 __global__ void k_check_batch(const int32_t *__restrict__ eoff, const int32_t *__restrict__ noff, int32_t k,
                               int64_t m, int32_t n, int32_t *__restrict__ bad, int32_t *__restrict__ status) {
+    pdl_prologue();
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < k; i += int64_t(gridDim.x) * blockDim.x) {
         const bool ok = eoff[i] >= 0 && eoff[i] <= eoff[i + 1] && eoff[i + 1] <= m && noff[i] >= 0 &&
                         noff[i] < noff[i + 1] && noff[i + 1] <= n && (i > 0 || (eoff[0] == 0 && noff[0] == 0)) &&
@@ -703,6 +731,7 @@ __global__ void k_check_batch(const int32_t *__restrict__ eoff, const int32_t *_
 __global__ void k_globalize(const int32_t *__restrict__ edges, int64_t m, const int32_t *__restrict__ eoff,
                             const int32_t *__restrict__ noff, int32_t k, const int32_t *__restrict__ bad,
                             int32_t *__restrict__ gedges, int32_t *__restrict__ status) {
+    pdl_prologue();
     const bool unusable = *bad != 0;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
         int32_t gu = -1, gv = -1;
@@ -763,9 +792,9 @@ extern "C" etl_status find_bridges_batch(const int32_t *edges, const int32_t *ed
     memset_async(bad, 0, sizeof(int32_t), s);
     {
         PhaseTimer pt("br.globalize", s);
-        k_check_batch<<<grid_for(k, 256), 256, 0, s>>>(edge_off, node_off, k, total_m, total_n, bad, st);
+        launch(k_check_batch, grid_for(k, 256), 256, 0, s, edge_off, node_off, k, total_m, total_n, bad, st);
         note_launch();
-        k_globalize<<<grid_for(total_m, 256), 256, 0, s>>>(edges, total_m, edge_off, node_off, k, bad, gedges, st);
+        launch(k_globalize, grid_for(total_m, 256), 256, 0, s, edges, total_m, edge_off, node_off, k, bad, gedges, st);
         note_launch();
     }
     etl_status rc = last_launch();
@@ -787,16 +816,16 @@ extern "C" etl_status two_edge_cc(const int32_t *edges, int64_t m, int32_t n, in
     if (rc) return rc;
     const int gn = grid_for(n, 256);
     PhaseTimer pt("br.two_edge_cc", s);
-    k_iota<<<gn, 256, 0, s>>>(n, label);
+    launch(k_iota, gn, 256, 0, s, n, label);
     note_launch();
     if (m > 0) {  // connected components of the graph without its bridges; labels = smallest vertex
-        k_hook<<<grid_for(m, kHookChunk), kHookChunk, 0, s>>>(edges, m, 0, hook_positions(m), false, n, label,
-                                                            nullptr, is_bridge, nullptr, st);
+        launch(k_hook, grid_for(m, kHookChunk), kHookChunk, 0, s, edges, m, 0, hook_positions(m), false, n, label,
+               nullptr, is_bridge, nullptr, st);
         note_launch();
-        k_compress<<<gn, 256, 0, s>>>(n, label, st);
+        launch(k_compress, gn, 256, 0, s, n, label, st);
         note_launch();
     }
-    k_labels_on_error<<<gn, 256, 0, s>>>(n, st, label);
+    launch(k_labels_on_error, gn, 256, 0, s, n, st, label);
     note_launch();
     return last_launch();
 }

@@ -122,6 +122,33 @@ inline etl_status last_launch() {
     return e == cudaSuccess ? ETL_OK : ETL_ECUDA;
 }
 
+// Programmatic dependent launch (ETL_TUNE_PDL). Every kernel of the library starts with
+// pdl_prologue(): it waits until the grid launched before it on the stream has finished and its
+// writes are visible (a no-op when the kernel was not launched as a dependent), then allows the
+// next grid on the stream to be scheduled. launch() issues a kernel with the attribute when the knob
+// is on, so the next kernel's launch overlaps the end of the current one instead of following it.
+bool &pdl_enabled();
+
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 inline int ceil_log2(uint64_t x) {  // smallest b with 2^b >= x (x >= 1)

@@ -43,6 +43,7 @@ __device__ __forceinline__ uint32_t lowbit(uint32_t x) { return x & (0u - x); }
 
 __global__ void k_inlabel(const int32_t *__restrict__ pre, const int32_t *__restrict__ size, int32_t n,
                           uint32_t *__restrict__ inl) {
+    pdl_prologue();
     for (int64_t v = gtid(); v < n; v += gstride()) {
         const int32_t p = pre[v], sz = size[v];
         if (p < 0 || sz < 1 || int64_t(p) + sz > n) {  // only on a tree the handle already flagged as bad
@@ -61,6 +62,7 @@ __global__ void k_inlabel_heads(const int32_t *__restrict__ parent, const int32_
                                 const int32_t *__restrict__ depth, const int32_t *__restrict__ size,
                                 const uint32_t *__restrict__ inl, int32_t n, int32_t *__restrict__ tourval,
                                 int2 *__restrict__ pathrec) {
+    pdl_prologue();
     for (int64_t v = gtid(); v < n; v += gstride()) {
         const int32_t p = parent[v];
         const uint32_t iv = inl[v];
@@ -78,6 +80,7 @@ __global__ void k_inlabel_heads(const int32_t *__restrict__ parent, const int32_
 __global__ void k_inlabel_records(const uint32_t *__restrict__ inl, const int32_t *__restrict__ pre,
                                   const int32_t *__restrict__ depth, const int32_t *__restrict__ parent,
                                   const int32_t *__restrict__ excl, int32_t n, int4 *__restrict__ rec) {
+    pdl_prologue();
     for (int64_t v = gtid(); v < n; v += gstride()) {
         const int64_t open = 2 * int64_t(pre[v]) - depth[v];
         const int32_t asc = (open >= 0 && open < 2 * int64_t(n)) ? excl[open + 1] : 0;  // inclusive prefix at open
@@ -99,6 +102,7 @@ __device__ __forceinline__ uint32_t label_at(uint32_t x, int k) {  // ancestor o
 __global__ void __launch_bounds__(256)
     k_inlabel_query(InView h, const int32_t *__restrict__ u, const int32_t *__restrict__ v, int64_t q,
                     int32_t *__restrict__ out, int32_t *__restrict__ status) {
+    pdl_prologue();
     const bool bad_tree = *h.hstatus != 0;
     for (int64_t i = gtid(); i < q; i += gstride()) {
         const int32_t x = __ldcs(u + i), y = __ldcs(v + i);
@@ -174,18 +178,18 @@ etl_status lca_build_inlabel_impl(etl_lca_t h, const int32_t *parent, cudaStream
     const int g = grid_for(n, 256);
     {
         PhaseTimer pt("inlabel.build", s);
-        k_inlabel<<<g, 256, 0, s>>>(h->pre, h->size, n, inl);
+        launch(k_inlabel, g, 256, 0, s, h->pre, h->size, n, inl);
         note_launch();
-        k_inlabel_heads<<<g, 256, 0, s>>>(parent, h->pre, h->depth, h->size, inl, n, tourval,
-                                          reinterpret_cast<int2 *>(h->inpath));
+        launch(k_inlabel_heads, g, 256, 0, s, parent, h->pre, h->depth, h->size, inl, n, tourval,
+               reinterpret_cast<int2 *>(h->inpath));
         note_launch();
     }
     etl_status st = last_launch();
     if (!st) st = scan_exclusive_i32(tourval, excl, 2 * int64_t(n), ws);
     if (!st) {
         PhaseTimer pt("inlabel.build", s);
-        k_inlabel_records<<<g, 256, 0, s>>>(inl, h->pre, h->depth, parent, excl, n,
-                                            reinterpret_cast<int4 *>(h->inrec));
+        launch(k_inlabel_records, g, 256, 0, s, inl, h->pre, h->depth, parent, excl, n,
+               reinterpret_cast<int4 *>(h->inrec));
         note_launch();
         st = last_launch();
     }
@@ -206,7 +210,7 @@ extern "C" etl_status lca_query_inlabel(etl_lca_t h, const int32_t *u, const int
     InView view{h->n, reinterpret_cast<const int4 *>(h->inrec), reinterpret_cast<const int2 *>(h->inpath),
                 h->status};
     PhaseTimer pt("inlabel.query", s);
-    k_inlabel_query<<<grid_for(q, 256), 256, 0, s>>>(view, u, v, q, out, status);
+    launch(k_inlabel_query, grid_for(q, 256), 256, 0, s, view, u, v, q, out, status);
     note_launch();
     return last_launch();
 }

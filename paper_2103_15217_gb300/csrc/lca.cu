@@ -51,6 +51,7 @@ __device__ __forceinline__ int64_t gstride() { return int64_t(gridDim.x) * block
 // node_off must be 0 = off[0] < off[1] < ... < off[k] = total (every instance non-empty)
 __global__ void k_check_offsets(const int32_t *__restrict__ off, int32_t k, int32_t total,
                                 int32_t *__restrict__ bad, int32_t *__restrict__ status) {
+    pdl_prologue();
     for (int64_t i = gtid(); i < k; i += gstride()) {
         const int32_t b = off[i], e = off[i + 1];
         if (b < 0 || e > total || b >= e || (i == 0 && b != 0) || (i == k - 1 && e != total)) {
@@ -63,6 +64,7 @@ __global__ void k_check_offsets(const int32_t *__restrict__ off, int32_t k, int3
 // inst_of[v] = instance of node v; one block per instance, coalesced writes
 __global__ void k_fill_inst(const int32_t *__restrict__ off, int32_t k, const int32_t *__restrict__ bad,
                             int32_t *__restrict__ inst_of) {
+    pdl_prologue();
     if (*bad) return;
     for (int64_t i = blockIdx.x; i < k; i += gridDim.x) {
         const int32_t b = off[i], e = off[i + 1];
@@ -76,6 +78,7 @@ __global__ void k_count_children(const int32_t *__restrict__ parent, int32_t n, 
                                  int32_t *__restrict__ gparent, int32_t *__restrict__ cnt,
                                  int32_t *__restrict__ root_cnt, int32_t *__restrict__ root_of,
                                  int32_t *__restrict__ status) {
+    pdl_prologue();
     const bool bad_offsets = BATCH && *bad;
     for (int64_t t = gtid(); t < n; t += gstride()) {
         const int32_t v = int32_t(t);
@@ -115,6 +118,7 @@ __global__ void k_count_children(const int32_t *__restrict__ parent, int32_t n, 
 // k_tour_assemble interleaves the two.
 __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restrict__ coff, int32_t n,
                             int32_t *__restrict__ so, int32_t *__restrict__ sc) {
+    pdl_prologue();
     const int32_t kept = coff[n];  // number of (parent, child) pairs
     for (int64_t t = gtid(); t < n; t += gstride()) {
         const int32_t v = int32_t(t);
@@ -141,6 +145,7 @@ __global__ void k_tour_succ(const int2 *__restrict__ kv, const int32_t *__restri
 __global__ void k_tour_assemble(const int32_t *__restrict__ coff, const int32_t *__restrict__ par,
                                 const int32_t *__restrict__ so, const int32_t *__restrict__ sc, int32_t n,
                                 int32_t *__restrict__ succ) {
+    pdl_prologue();
     int2 *pair = reinterpret_cast<int2 *>(succ);
     for (int64_t t = gtid(); t < n; t += gstride()) {
         const bool leaf = __ldcs(coff + t) == __ldcs(coff + t + 1) && __ldcs(par + t) >= 0;  // no children, no root
@@ -155,6 +160,7 @@ __global__ void k_tour_assemble(const int32_t *__restrict__ coff, const int32_t 
 __global__ void k_link_roots(const int32_t *__restrict__ root_cnt, const int32_t *__restrict__ root_of, int32_t k,
                              int32_t n, int32_t *__restrict__ sc, int32_t *__restrict__ head,
                              int32_t *__restrict__ status) {
+    pdl_prologue();
     if (gtid() == 0) *head = 2 * root_of[0];
     for (int64_t i = gtid(); i < k; i += gstride()) {
         if (root_cnt[i] != 1) set_status(status, ETL_EBADTREE);
@@ -168,6 +174,7 @@ __global__ void k_link_roots(const int32_t *__restrict__ root_cnt, const int32_t
 __global__ void k_node_stats(RankResult rr, const int32_t *__restrict__ succ, int32_t n, int32_t *__restrict__ pre,
                              int32_t *__restrict__ depth, int32_t *__restrict__ size, int32_t *__restrict__ order,
                              int32_t *__restrict__ status) {
+    pdl_prologue();
     const uint4 *pk = reinterpret_cast<const uint4 *>(rr.packed);  // brackets 2v and 2v+1 side by side
     for (int64_t t = gtid(); t < n; t += gstride()) {
         const bool leaf = __ldcs(succ + 2 * t) < ETL_END;  // contracted: the closing bracket is ranked right after
@@ -200,6 +207,7 @@ constexpr int kGatherIlp = 4;  // positions per thread per step whose dependent 
 
 __global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *__restrict__ pre,
                              const int32_t *__restrict__ order, int32_t n, int32_t *__restrict__ q0) {
+    pdl_prologue();
     const int64_t step = gstride() * kGatherIlp;
     for (int64_t base = blockIdx.x * int64_t(blockDim.x) * kGatherIlp + threadIdx.x; base < n; base += step) {
         int32_t v[kGatherIlp], p[kGatherIlp];
@@ -222,6 +230,7 @@ __global__ void k_parent_pre(const int32_t *__restrict__ parent, const int32_t *
 __global__ void k_check_instances(const int32_t *__restrict__ root_of, const int32_t *__restrict__ off, int32_t k,
                                   int32_t n, const int32_t *__restrict__ pre, const int32_t *__restrict__ size,
                                   int32_t *__restrict__ status) {
+    pdl_prologue();
     for (int64_t i = gtid(); i < k; i += gstride()) {
         const int32_t b = off ? off[i] : 0, e = off ? off[i + 1] : n;
         const int32_t r = root_of[i];
@@ -244,6 +253,7 @@ struct LcaView {
 // table stores (pm, sm) pairs, so this is one 8-byte gather per node.
 __global__ void k_node_rec(const int32_t *__restrict__ pre, const int32_t *__restrict__ size,
                            const int2 *__restrict__ pmsm, int32_t n, int4 *__restrict__ nrec) {
+    pdl_prologue();
     constexpr int kIlp = 4;  // nodes per thread per step, their gathers in flight together
     const int64_t step = gstride() * kIlp;
     for (int64_t base = blockIdx.x * int64_t(blockDim.x) * kIlp + threadIdx.x; base < n; base += step) {
@@ -279,6 +289,7 @@ template <bool BATCH, bool BLOCKED>
 __global__ void __launch_bounds__(256)
     k_lca_query(LcaView h, const int32_t *__restrict__ inst, const int32_t *__restrict__ u,
                 const int32_t *__restrict__ v, int64_t q, int32_t *__restrict__ out, int32_t *__restrict__ status) {
+    pdl_prologue();
     const bool bad_tree = *h.hstatus != 0;
     const int64_t stride = gstride();
     for (int64_t base = gtid(); base < q; base += stride * kQueryIlp) {
@@ -436,16 +447,16 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
             memset_async(root_of, 0, size_t(k) * sizeof(int32_t), s);
             PhaseTimer pt("lca.count", s);
             if (batch) {
-                k_check_offsets<<<grid_for(k, 256), 256, 0, s>>>(h->node_off, k, n, misc + 1, h->status);
+                launch(k_check_offsets, grid_for(k, 256), 256, 0, s, h->node_off, k, n, misc + 1, h->status);
                 note_launch();
-                k_fill_inst<<<k < 8192 ? k : 8192, 256, 0, s>>>(h->node_off, k, misc + 1, inst_of);
+                launch(k_fill_inst, k < 8192 ? k : 8192, 256, 0, s, h->node_off, k, misc + 1, inst_of);
                 note_launch();
-                k_count_children<true><<<grid_for(n, 256), 256, 0, s>>>(parent, n, h->node_off, inst_of, misc + 1,
-                                                                        gparent, cnt, root_cnt, root_of, h->status);
+                launch(k_count_children<true>, grid_for(n, 256), 256, 0, s, parent, n, h->node_off, inst_of, misc + 1,
+                       gparent, cnt, root_cnt, root_of, h->status);
                 note_launch();
             } else {
-                k_count_children<false><<<grid_for(n, 256), 256, 0, s>>>(parent, n, nullptr, nullptr, nullptr,
-                                                                         nullptr, cnt, root_cnt, root_of, h->status);
+                launch(k_count_children<false>, grid_for(n, 256), 256, 0, s, parent, n, nullptr, nullptr, nullptr,
+                       nullptr, cnt, root_cnt, root_of, h->status);
                 note_launch();
             }
             st = last_launch();
@@ -456,11 +467,11 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
         if (!st) {
             PhaseTimer pt("lca.succ", s);
             int32_t *so = cnt;  // the child counts are no longer needed once the offsets are scanned
-            k_tour_succ<<<grid_for(n, 256), 256, 0, s>>>(sr.kv, coff, n, so, sc);
+            launch(k_tour_succ, grid_for(n, 256), 256, 0, s, sr.kv, coff, n, so, sc);
             note_launch();
-            k_link_roots<<<grid_for(k, 256), 256, 0, s>>>(root_cnt, root_of, k, n, sc, misc, h->status);
+            launch(k_link_roots, grid_for(k, 256), 256, 0, s, root_cnt, root_of, k, n, sc, misc, h->status);
             note_launch();
-            k_tour_assemble<<<grid_for(n, 256), 256, 0, s>>>(coff, par, so, sc, n, succ);
+            launch(k_tour_assemble, grid_for(n, 256), 256, 0, s, coff, par, so, sc, n, succ);
             note_launch();
             st = last_launch();
         }
@@ -468,17 +479,17 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
         if (!st) st = list_rank(succ, 2 * int64_t(n), nullptr, misc, true, 2 * int64_t(n), h->status, ws, &rr);
         if (!st) {
             PhaseTimer pt("lca.node_stats", s);
-            k_node_stats<<<grid_for(n, 256), 256, 0, s>>>(rr, succ, n, h->pre, h->depth, h->size, h->order,
-                                                          h->status);
+            launch(k_node_stats, grid_for(n, 256), 256, 0, s, rr, succ, n, h->pre, h->depth, h->size, h->order,
+                   h->status);
             note_launch();
-            k_check_instances<<<grid_for(k, 256), 256, 0, s>>>(root_of, batch ? h->node_off : nullptr, k, n, h->pre,
-                                                                h->size, h->status);
+            launch(k_check_instances, grid_for(k, 256), 256, 0, s, root_of, batch ? h->node_off : nullptr, k, n, h->pre,
+                   h->size, h->status);
             note_launch();
             st = last_launch();
         }
         if (!st && with_table) {
             PhaseTimer pt("lca.parent_pre", s);
-            k_parent_pre<<<grid_for(n, 256), 256, 0, s>>>(par, h->pre, h->order, n, h->table);
+            launch(k_parent_pre, grid_for(n, 256), 256, 0, s, par, h->pre, h->order, n, h->table);
             note_launch();
             st = last_launch();
         }
@@ -487,9 +498,8 @@ etl_status lca_build(const int32_t *parent, int32_t n, const int32_t *node_off, 
                             : sparse_table_build<false>(h->table, n, h->levels, s);
         if (!st && with_table && h->blocked) {
             PhaseTimer pt("lca.node_rec", s);
-            k_node_rec<<<grid_for(n, 256), 256, 0, s>>>(
-                h->pre, h->size, reinterpret_cast<const int2 *>(h->table + h->bl.nblk * kRmqBlock), n,
-                static_cast<int4 *>(h->nrec));
+            launch(k_node_rec, grid_for(n, 256), 256, 0, s, h->pre, h->size,
+                   reinterpret_cast<const int2 *>(h->table + h->bl.nblk * kRmqBlock), n, static_cast<int4 *>(h->nrec));
             note_launch();
             st = last_launch();
         }
@@ -513,14 +523,14 @@ etl_status query_launch(etl_lca_t h, const int32_t *inst, const int32_t *u, cons
     const int grid = grid_for(ceil_div(q, kQueryIlp), 256);
     if (h->blocked) {
         if (inst)
-            k_lca_query<true, true><<<grid, 256, 0, s>>>(view, inst, u, v, q, out, status);
+            launch(k_lca_query<true, true>, grid, 256, 0, s, view, inst, u, v, q, out, status);
         else
-            k_lca_query<false, true><<<grid, 256, 0, s>>>(view, nullptr, u, v, q, out, status);
+            launch(k_lca_query<false, true>, grid, 256, 0, s, view, nullptr, u, v, q, out, status);
     } else {
         if (inst)
-            k_lca_query<true, false><<<grid, 256, 0, s>>>(view, inst, u, v, q, out, status);
+            launch(k_lca_query<true, false>, grid, 256, 0, s, view, inst, u, v, q, out, status);
         else
-            k_lca_query<false, false><<<grid, 256, 0, s>>>(view, nullptr, u, v, q, out, status);
+            launch(k_lca_query<false, false>, grid, 256, 0, s, view, nullptr, u, v, q, out, status);
     }
     note_launch();
     return last_launch();

@@ -32,6 +32,7 @@ __device__ __forceinline__ unsigned long long pack(int32_t anc, int32_t dist) {
 
 __global__ void k_naive_init(const int32_t *__restrict__ parent, int32_t n, unsigned long long *__restrict__ ad,
                              int32_t *__restrict__ level, int32_t *__restrict__ roots, int32_t *__restrict__ status) {
+    pdl_prologue();
     for (int64_t v = gtid(); v < n; v += gstride()) {
         const int32_t p = parent[v];
         if (p == -1) {
@@ -47,6 +48,7 @@ __global__ void k_naive_init(const int32_t *__restrict__ parent, int32_t n, unsi
 
 __global__ void k_naive_jump(int32_t n, unsigned long long *__restrict__ ad, int32_t *__restrict__ level,
                              int32_t *__restrict__ pending) {
+    pdl_prologue();
     for (int64_t v = gtid(); v < n; v += gstride()) {
         if (__ldcg(level + v) >= 0) continue;
         bool done = false;
@@ -70,6 +72,7 @@ __global__ void k_naive_jump(int32_t n, unsigned long long *__restrict__ ad, int
 __global__ void k_naive_records(const int32_t *__restrict__ parent, const int32_t *__restrict__ level, int32_t n,
                                 const int32_t *__restrict__ roots, int2 *__restrict__ rec,
                                 int32_t *__restrict__ status) {
+    pdl_prologue();
     if (gtid() == 0 && *roots != 1) set_status(status, ETL_EBADTREE);
     for (int64_t v = gtid(); v < n; v += gstride()) {
         const int32_t l = level[v];
@@ -81,6 +84,7 @@ __global__ void k_naive_records(const int32_t *__restrict__ parent, const int32_
 __global__ void __launch_bounds__(256)
     k_naive_query(const int2 *__restrict__ rec, int32_t n, const int32_t *__restrict__ u,
                   const int32_t *__restrict__ v, int64_t q, int32_t *__restrict__ out, int32_t *__restrict__ status) {
+    pdl_prologue();
     for (int64_t i = gtid(); i < q; i += gstride()) {
         int32_t a = __ldcs(u + i), b = __ldcs(v + i);
         int32_t res = -1;
@@ -142,7 +146,7 @@ extern "C" etl_status lca_naive_preprocess(const int32_t *parent, int32_t n, int
     memset_async(cnt, 0, 2 * sizeof(int32_t), s);
     const int g = grid_for(n, 256);
     PhaseTimer pt("naive.levels", s);
-    k_naive_init<<<g, 256, 0, s>>>(parent, n, ad, level, cnt, st);
+    launch(k_naive_init, g, 256, 0, s, parent, n, ad, level, cnt, st);
     note_launch();
     // every jump adds at least the distance the ancestor covered at the end of the previous launch,
     // so launch r covers >= 6^r levels even with asynchronous jumps: ceil(log6 n) + 1 launches suffice
@@ -150,10 +154,10 @@ extern "C" etl_status lca_naive_preprocess(const int32_t *parent, int32_t n, int
     for (double c = 1; c < double(n); c *= (kJumpsPerLaunch + 1)) ++launches;
     for (int r = 0; r < launches; ++r) {
         if (r == launches - 1) memset_async(cnt + 1, 0, sizeof(int32_t), s);
-        k_naive_jump<<<g, 256, 0, s>>>(n, ad, level, cnt + 1);
+        launch(k_naive_jump, g, 256, 0, s, n, ad, level, cnt + 1);
         note_launch();
     }
-    k_naive_records<<<g, 256, 0, s>>>(parent, level, n, cnt, reinterpret_cast<int2 *>(rec), st);
+    launch(k_naive_records, g, 256, 0, s, parent, level, n, cnt, reinterpret_cast<int2 *>(rec), st);
     note_launch();
     return last_launch();
 }
@@ -165,7 +169,7 @@ extern "C" etl_status lca_naive_query(const int32_t *rec, int32_t n, const int32
     if (!u || !v || !out) return ETL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PhaseTimer pt("naive.query", s);
-    k_naive_query<<<grid_for(q, 256), 256, 0, s>>>(reinterpret_cast<const int2 *>(rec), n, u, v, q, out, status);
+    launch(k_naive_query, grid_for(q, 256), 256, 0, s, reinterpret_cast<const int2 *>(rec), n, u, v, q, out, status);
     note_launch();
     return last_launch();
 }

@@ -79,6 +79,7 @@ PhaseTimer::~PhaseTimer() {
 // walk over a list in random order. Indices outside [0, n) are skipped.
 __global__ void k_probe_gather_scatter(const int32_t *__restrict__ order, const int32_t *__restrict__ succ,
                                        int64_t n, uint2 *__restrict__ out) {
+    pdl_prologue();
     constexpr int kIlp = 4;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; base < n; base += stride * kIlp) {
@@ -112,7 +113,7 @@ extern "C" etl_status etl_probe_gather_scatter(const int32_t *order, const int32
     int64_t blocks = ceil_div(ceil_div(n, 4), 256);
     const int64_t cap = int64_t(num_sms()) * 8 * 4;  // four waves of full occupancy
     if (blocks > cap) blocks = cap;
-    k_probe_gather_scatter<<<int(blocks), 256, 0, s>>>(order, succ, n, static_cast<uint2 *>(out));
+    launch(k_probe_gather_scatter, int(blocks), 256, 0, s, order, succ, n, static_cast<uint2 *>(out));
     note_launch();
     return last_launch();
 }

@@ -78,6 +78,7 @@ __global__ void k_walk0(const int32_t *__restrict__ succ, int64_t len, const int
                         uint2 *__restrict__ packed, int32_t *__restrict__ rnext, int32_t *__restrict__ rw1,
                         int32_t *__restrict__ rw2, int32_t *__restrict__ ctr, int32_t dyn_cap,
                         int32_t *__restrict__ next_head, int32_t *__restrict__ status) {
+    pdl_prologue();
     const int32_t head = *d_head;
     const bool head_split = H.split(uint32_t(head));
     if (blockIdx.x == 0 && threadIdx.x == 0) *next_head = head_split ? H.sid(uint32_t(head)) : int32_t(H.S0);
@@ -173,6 +174,7 @@ __global__ void k_walk(const int32_t *__restrict__ succ, const int32_t *__restri
                        int32_t *__restrict__ rnext, int32_t *__restrict__ rw1, int32_t *__restrict__ rw2,
                        int32_t *__restrict__ ctr, int32_t dyn_cap, int32_t *__restrict__ next_head,
                        int32_t *__restrict__ status) {
+    pdl_prologue();
     const int64_t len = level_len(len_base, d_len_add, cap);
     const int32_t head = *d_head;
     const bool head_split = H.split(uint32_t(head));
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(kPjThreads)
                    int64_t len_base, const int32_t *__restrict__ d_len_add, int64_t cap,
                    const int32_t *__restrict__ d_head, int64_t expect_total, int32_t *__restrict__ R,
                    int32_t *__restrict__ O, int32_t *__restrict__ status) {
+    pdl_prologue();
     extern __shared__ int32_t sm[];
     int32_t *Q = sm, *V1 = sm + kPjCap, *V2 = sm + 2 * kPjCap, *F = sm + 3 * kPjCap;
     __shared__ int found;
@@ -330,6 +333,7 @@ __global__ void __launch_bounds__(kPjThreads)
 __global__ void k_expand(const int4 *__restrict__ loc, int64_t len_base, const int32_t *__restrict__ d_len_add,
                          int64_t cap, int64_t up_cap, const int32_t *__restrict__ Rup,
                          const int32_t *__restrict__ Oup, int32_t *__restrict__ R, int32_t *__restrict__ O) {
+    pdl_prologue();
     const int64_t len = level_len(len_base, d_len_add, cap);
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
         const int4 l = loc[e];
@@ -340,10 +344,14 @@ __global__ void k_expand(const int4 *__restrict__ loc, int64_t len_base, const i
     }
 }
 
-__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
+__global__ void k_set_i32(int32_t *p, int32_t v) {
+    pdl_prologue();
+    *p = v;
+}
 
 __global__ void k_final_rank(const uint2 *__restrict__ packed, int64_t len, const int32_t *__restrict__ R,
                              int64_t rcap, int32_t *__restrict__ rank) {
+    pdl_prologue();
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
         const uint2 p = packed[e];
         rank[e] = p.x < rcap ? R[p.x] + int32_t(p.y & 0xffffu) : -1;
@@ -407,11 +415,11 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
         PhaseTimer pt0("rank.walk0", s);
         const int grid = walk_grid(len0, 12, int64_t(H.S0) + 1, P);
         if (dual)
-            k_walk0<true><<<grid, P.block, 0, s>>>(succ, len0, d_head, H, packed, rnext, rw1, rw2, ctr, dyn_cap, head1,
-                                                    status);
+            launch(k_walk0<true>, grid, P.block, 0, s, succ, len0, d_head, H, packed, rnext, rw1, rw2, ctr, dyn_cap,
+                   head1, status);
         else
-            k_walk0<false><<<grid, P.block, 0, s>>>(succ, len0, d_head, H, packed, rnext, rw1, rw2, ctr, dyn_cap,
-                                                     head1, status);
+            launch(k_walk0<false>, grid, P.block, 0, s, succ, len0, d_head, H, packed, rnext, rw1, rw2, ctr, dyn_cap,
+                   head1, status);
         note_launch();
         st = last_launch();
     }
@@ -442,8 +450,8 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
         {
             PhaseTimer ptw("rank.walk", s);
             const int grid = walk_grid(L.cap, 28, int64_t(h.S0) + 1, P);
-            k_walk<<<grid, P.block, 0, s>>>(L.succ, L.w1, L.w2, L.base, L.d_add, L.cap, L.d_head, h, L.loc, nn, n1, n2,
-                                            c, dcap, hd, status);
+            launch(k_walk, grid, P.block, 0, s, L.succ, L.w1, L.w2, L.base, L.d_add, L.cap, L.d_head, h, L.loc, nn, n1,
+                   n2, c, dcap, hd, status);
         note_launch();
             st = last_launch();
         }
@@ -458,8 +466,8 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
         T.O = ws.get<int32_t>(T.cap);
         if (!ws.ok()) return ETL_ENOMEM;
         PhaseTimer ptp("rank.pj", s);
-        k_pointer_jump<<<1, kPjThreads, 4 * kPjCap * 4, s>>>(T.succ, T.w1, T.w2, T.base, T.d_add, T.cap, T.d_head,
-                                                              expect_len, T.R, T.O, status);
+        launch(k_pointer_jump, 1, kPjThreads, 4 * kPjCap * 4, s, T.succ, T.w1, T.w2, T.base, T.d_add, T.cap, T.d_head,
+               expect_len, T.R, T.O, status);
         note_launch();
         st = last_launch();
         if (st) return st;
@@ -473,8 +481,8 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
         int blocks = int(ceil_div(L.cap, 256));
         if (blocks > num_sms() * 32) blocks = num_sms() * 32;  // four waves of full occupancy
         PhaseTimer pte("rank.expand", s);
-        k_expand<<<blocks, 256, 0, s>>>(L.loc, L.base, L.d_add, L.cap, lv[i + 1].cap, lv[i + 1].R, lv[i + 1].O, L.R,
-                                        L.O);
+        launch(k_expand, blocks, 256, 0, s, L.loc, L.base, L.d_add, L.cap, lv[i + 1].cap, lv[i + 1].R, lv[i + 1].O, L.R,
+               L.O);
         note_launch();
         st = last_launch();
         if (st) return st;
@@ -487,7 +495,7 @@ etl_status list_rank(const int32_t *succ, int64_t n_cap, const int32_t *d_len, c
 }
 
 etl_status set_device_i32(int32_t *p, int32_t v, cudaStream_t s) {
-    k_set_i32<<<1, 1, 0, s>>>(p, v);
+    launch(k_set_i32, 1, 1, 0, s, p, v);
         note_launch();
     return last_launch();
 }
@@ -498,7 +506,7 @@ etl_status final_rank(const RankResult &r, int64_t len, int32_t *rank, cudaStrea
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     PhaseTimer pt("rank.final", s);
-    k_final_rank<<<blocks, 256, 0, s>>>(r.packed, len, r.R, r.rcap, rank);
+    launch(k_final_rank, blocks, 256, 0, s, r.packed, len, r.R, r.rcap, rank);
         note_launch();
     return last_launch();
 }
@@ -638,9 +646,9 @@ extern "C" etl_status etl_list_rank_static(const int32_t *succ, int64_t len, int
 
     if (!status && cudaMemsetAsync(st, 0, sizeof(int32_t), s) != cudaSuccess) return ETL_ECUDA;
     if (cudaMemsetAsync(ctr, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return ETL_ECUDA;
-    k_set_i32<<<1, 1, 0, s>>>(word, head);
+    launch(k_set_i32, 1, 1, 0, s, word, head);
     note_launch();
-    k_walk0<false><<<grid, block, 0, s>>>(succ, len, word, H, packed, rnext, rw1, rw2, ctr, dyn_cap, head1, st);
+    launch(k_walk0<false>, grid, block, 0, s, succ, len, word, H, packed, rnext, rw1, rw2, ctr, dyn_cap, head1, st);
     note_launch();
     if ((rc = last_launch())) return rc;
 
@@ -666,8 +674,8 @@ extern "C" etl_status etl_list_rank_static(const int32_t *succ, int64_t len, int
         if (!L.loc || !nn || !n1 || !n2 || !c || !hd) return ETL_ENOMEM;
         if (cudaMemsetAsync(c, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return ETL_ECUDA;
         if (cudaMemsetAsync(L.loc, 0xff, size_t(L.cap) * sizeof(int4), s) != cudaSuccess) return ETL_ECUDA;
-        k_walk<<<grid, block, 0, s>>>(L.succ, L.w1, L.w2, L.base, L.d_add, L.cap, L.d_head, h, L.loc, nn, n1, n2, c,
-                                      dcap, hd, st);
+        launch(k_walk, grid, block, 0, s, L.succ, L.w1, L.w2, L.base, L.d_add, L.cap, L.d_head, h, L.loc, nn, n1, n2, c,
+               dcap, hd, st);
         note_launch();
         if ((rc = last_launch())) return rc;
         lv[nl++] = Level{nn, n1, n2, int64_t(h.S0) + 1, ncap, c + 1, hd, nullptr, nullptr, nullptr};
@@ -676,8 +684,8 @@ extern "C" etl_status etl_list_rank_static(const int32_t *succ, int64_t len, int
     T.R = A.take<int32_t>(T.cap);
     T.O = A.take<int32_t>(T.cap);
     if (!T.R || !T.O) return ETL_ENOMEM;
-    k_pointer_jump<<<1, kPjThreads, 4 * kPjCap * 4, s>>>(T.succ, T.w1, T.w2, T.base, T.d_add, T.cap, T.d_head, len,
-                                                          T.R, T.O, st);
+    launch(k_pointer_jump, 1, kPjThreads, 4 * kPjCap * 4, s, T.succ, T.w1, T.w2, T.base, T.d_add, T.cap, T.d_head, len,
+           T.R, T.O, st);
     note_launch();
     if ((rc = last_launch())) return rc;
     for (int i = nl - 2; i >= 0; --i) {
@@ -687,14 +695,14 @@ extern "C" etl_status etl_list_rank_static(const int32_t *succ, int64_t len, int
         if (!L.R || !L.O) return ETL_ENOMEM;
         int blocks = int(ceil_div(L.cap, 256));
         if (blocks > grid * 4) blocks = grid * 4;
-        k_expand<<<blocks, 256, 0, s>>>(L.loc, L.base, L.d_add, L.cap, lv[i + 1].cap, lv[i + 1].R, lv[i + 1].O, L.R,
-                                        L.O);
+        launch(k_expand, blocks, 256, 0, s, L.loc, L.base, L.d_add, L.cap, lv[i + 1].cap, lv[i + 1].R, lv[i + 1].O, L.R,
+               L.O);
         note_launch();
         if ((rc = last_launch())) return rc;
     }
     int blocks = int(ceil_div(len, 256));
     if (blocks > num_sms() * 16) blocks = num_sms() * 16;
-    k_final_rank<<<blocks, 256, 0, s>>>(packed, len, lv[0].R, lv[0].cap, rank);
+    launch(k_final_rank, blocks, 256, 0, s, packed, len, lv[0].R, lv[0].cap, rank);
     note_launch();
     return last_launch();
 }

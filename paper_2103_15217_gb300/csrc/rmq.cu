@@ -50,6 +50,7 @@ __device__ __forceinline__ int4 shifted(const int4 *__restrict__ p, int64_t i, i
 
 template <bool IS_MAX>
 __global__ void __launch_bounds__(1024) k_levels(int32_t *__restrict__ table, int64_t ld, int l, int count) {
+    pdl_prologue();
     const int4 *p = reinterpret_cast<const int4 *>(table + int64_t(l - 1) * ld);
     int4 *o0 = reinterpret_cast<int4 *>(table + int64_t(l) * ld);
     int4 *o1 = reinterpret_cast<int4 *>(table + int64_t(l + 1) * ld);
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(1024) k_levels(int32_t *__restrict__ table, in
 
 template <bool IS_MAX>
 __global__ void k_pad(int32_t *__restrict__ table, int64_t n, int64_t ld) {
+    pdl_prologue();
     const int64_t i = n + threadIdx.x;
     if (i < ld) table[i] = IS_MAX ? INT_MIN : INT_MAX;
 }
@@ -96,6 +98,7 @@ __device__ __forceinline__ int2 shfl_down(int2 v, int d) {
 template <class Op, bool PAIRS>
 __global__ void k_block_scan(typename Op::T *__restrict__ x, int64_t n, int64_t nblk, typename Op::T *__restrict__ pm,
                              typename Op::T *__restrict__ sm, typename Op::T *__restrict__ top0) {
+    pdl_prologue();
     using T = typename Op::T;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -128,6 +131,7 @@ __global__ void k_block_scan(typename Op::T *__restrict__ x, int64_t n, int64_t 
 // levels l .. l + count - 1 of the top table from level l - 1 (rows nblk apart, count <= 3)
 template <class Op>
 __global__ void k_top_levels(typename Op::T *__restrict__ top, int64_t nblk, int l, int count) {
+    pdl_prologue();
     using T = typename Op::T;
     const T *p = top + int64_t(l - 1) * nblk;
     const int64_t h = int64_t(1) << (l - 1);
@@ -165,11 +169,11 @@ etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L
         bool launched = false;
         if constexpr (std::is_same<T, int32_t>::value) {
             if (pairs) {
-                k_block_scan<Op, true><<<blocks, 256, 0, s>>>(base, n, L.nblk, base + N, base + 2 * N, top);
+                launch(k_block_scan<Op, true>, blocks, 256, 0, s, base, n, L.nblk, base + N, base + 2 * N, top);
                 launched = true;
             }
         }
-        if (!launched) k_block_scan<Op, false><<<blocks, 256, 0, s>>>(base, n, L.nblk, base + N, base + 2 * N, top);
+        if (!launched) launch(k_block_scan<Op, false>, blocks, 256, 0, s, base, n, L.nblk, base + N, base + 2 * N, top);
         note_launch();
     }
     etl_status st = last_launch();
@@ -178,7 +182,7 @@ etl_status blocked_build(typename Op::T *base, int64_t n, const BlockedLayout &L
         int blocks = int(ceil_div(L.nblk, 256));
         if (blocks > grid_cap) blocks = grid_cap;
         PhaseTimer pt("rmq.top", s);
-        k_top_levels<Op><<<blocks, 256, 0, s>>>(top, L.nblk, l, count);
+        launch(k_top_levels<Op>, blocks, 256, 0, s, top, L.nblk, l, count);
         note_launch();
         st = last_launch();
         l += count;
@@ -210,7 +214,7 @@ template <bool IS_MAX>
 etl_status sparse_table_build(int32_t *table, int64_t n, int levels, cudaStream_t s) {
     const int64_t ld = sparse_ld(n);
     if (ld > n) {
-        k_pad<IS_MAX><<<1, 4, 0, s>>>(table, n, ld);
+        launch(k_pad<IS_MAX>, 1, 4, 0, s, table, n, ld);
         note_launch();
     }
     const RmqParams &R = rmq_params();
@@ -226,7 +230,7 @@ etl_status sparse_table_build(int32_t *table, int64_t n, int levels, cudaStream_
         if (blocks > grid_cap) blocks = grid_cap;
         if (blocks < 1) blocks = 1;
         PhaseTimer pt(IS_MAX ? "rmq.level_max" : "rmq.level_min", s);
-        k_levels<IS_MAX><<<blocks, R.block, 0, s>>>(table, ld, l, count);
+        launch(k_levels<IS_MAX>, blocks, R.block, 0, s, table, ld, l, count);
         note_launch();
         etl_status st = last_launch();
         if (st) return st;

@@ -30,6 +30,7 @@ __device__ __forceinline__ int64_t eff_len(int64_t n, const int32_t *d_n) {
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_reduce(const T *__restrict__ in, int64_t n, const int32_t *d_n,
                                                      int32_t *__restrict__ partial) {
+    pdl_prologue();
     __shared__ int32_t wsum[kWarps];
     const int64_t nn = eff_len<T>(n, d_n);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -55,6 +56,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads)
     k_scan_tile(const T *__restrict__ in, int32_t *__restrict__ out, int64_t n, const int32_t *d_n,
                 const int32_t *__restrict__ offs, int64_t nblocks) {
+    pdl_prologue();
     __shared__ int32_t wsum[kWarps];
     const int64_t nn = eff_len<T>(n, d_n);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -102,6 +104,7 @@ static_assert(kSmallWarps == kWarp, "the warp totals are scanned by one warp");
 template <class T>
 __global__ void __launch_bounds__(kSmallThreads)
     k_scan_small(const T *__restrict__ in, int32_t *__restrict__ out, int64_t n, const int32_t *d_n) {
+    pdl_prologue();
     __shared__ int32_t wsum[kSmallWarps], wpre[kSmallWarps];
     __shared__ int32_t total;
     const int64_t nn = eff_len<T>(n, d_n);
@@ -144,25 +147,25 @@ etl_status scan_impl(const T *in, int32_t *out, int64_t n, const int32_t *d_n, W
     }
     int64_t nb = ceil_div(n, kTile);
     if (nb == 1) {
-        k_scan_tile<T><<<1, kThreads, 0, s>>>(in, out, n, d_n, nullptr, 1);
+        launch(k_scan_tile<T>, 1, kThreads, 0, s, in, out, n, d_n, nullptr, 1);
         note_launch();
         return last_launch();
     }
     if (n <= kSmallMax) {
-        k_scan_small<T><<<1, kSmallThreads, 0, s>>>(in, out, n, d_n);
+        launch(k_scan_small<T>, 1, kSmallThreads, 0, s, in, out, n, d_n);
         note_launch();
         return last_launch();
     }
     int32_t *partial = ws.get<int32_t>(nb);
     int32_t *pscan = ws.get<int32_t>(nb + 1);
     if (!ws.ok()) return ETL_ENOMEM;
-    k_reduce<T><<<unsigned(nb), kThreads, 0, s>>>(in, n, d_n, partial);
+    launch(k_reduce<T>, unsigned(nb), kThreads, 0, s, in, n, d_n, partial);
     note_launch();
     etl_status st = last_launch();
     if (st) return st;
     st = scan_impl<int32_t>(partial, pscan, nb, nullptr, ws);
     if (st) return st;
-    k_scan_tile<T><<<unsigned(nb), kThreads, 0, s>>>(in, out, n, d_n, pscan, nb);
+    launch(k_scan_tile<T>, unsigned(nb), kThreads, 0, s, in, out, n, d_n, pscan, nb);
     note_launch();
     return last_launch();
 }

@@ -39,6 +39,7 @@ template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_hist(const int32_t *__restrict__ keys, const int2 *__restrict__ kv, const int32_t *d_count, int64_t n_cap,
            int shift, int32_t key_limit, int32_t *__restrict__ ghist, int nblocks) {
+    pdl_prologue();
     constexpr int kRounds = R, kWarpTile = kWarp * R, kTile = kWarps * kWarpTile;
     __shared__ int32_t h[kRadix];
     const int64_t count = count_of(d_count, n_cap);
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(kThreads)
     k_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, const int2 *__restrict__ kv,
               const int32_t *d_count, int64_t n_cap, int shift, int32_t key_limit, const int32_t *__restrict__ goff,
               int nblocks, int2 *__restrict__ kv_out) {
+    pdl_prologue();
     constexpr int kRounds = R, kWarpTile = kWarp * R, kTile = kWarps * kWarpTile;
     __shared__ int32_t wcnt[kWarps][kRadix];
     __shared__ int32_t gbase[kRadix];
@@ -192,7 +194,7 @@ etl_status radix_sort_impl(const int32_t *keys_in, const int32_t *vals_in, const
         etl_status st;
         {
             PhaseTimer pt("sort.hist", s);
-            k_hist<R><<<nblocks, kThreads, 0, s>>>(keys_in, kvin, cnt, cap, shift, key_limit, ghist, nblocks);
+            launch(k_hist<R>, nblocks, kThreads, 0, s, keys_in, kvin, cnt, cap, shift, key_limit, ghist, nblocks);
             note_launch();
             st = last_launch();
         }
@@ -203,11 +205,11 @@ etl_status radix_sort_impl(const int32_t *keys_in, const int32_t *vals_in, const
         {
             PhaseTimer pt("sort.scatter", s);
             if (sort_params().ballot)
-                k_scatter<R, true><<<nblocks, kThreads, 0, s>>>(keys_in, vals_in, kvin, cnt, cap, shift, key_limit,
-                                                                goff, nblocks, out_kv);
+                launch(k_scatter<R, true>, nblocks, kThreads, 0, s, keys_in, vals_in, kvin, cnt, cap, shift, key_limit,
+                       goff, nblocks, out_kv);
             else
-                k_scatter<R, false><<<nblocks, kThreads, 0, s>>>(keys_in, vals_in, kvin, cnt, cap, shift, key_limit,
-                                                                 goff, nblocks, out_kv);
+                launch(k_scatter<R, false>, nblocks, kThreads, 0, s, keys_in, vals_in, kvin, cnt, cap, shift, key_limit,
+                       goff, nblocks, out_kv);
             note_launch();
             st = last_launch();
         }

@@ -35,6 +35,7 @@ __device__ __forceinline__ long long tour_key(int32_t depth, int32_t node) {
 __global__ void k_tour_keys(const int32_t *__restrict__ parent, const int32_t *__restrict__ pre,
                             const int32_t *__restrict__ depth, const int32_t *__restrict__ size, int32_t n,
                             long long *__restrict__ keys, int32_t *__restrict__ tpos) {
+    pdl_prologue();
     for (int64_t v = gtid(); v < n; v += gstride()) {
         const int32_t p = pre[v], d = depth[v], sz = size[v];
         const int64_t r0 = 2 * int64_t(p) - d, r1 = r0 + 2 * int64_t(sz) - 1;
@@ -60,6 +61,7 @@ constexpr int kIlp = 4;
 __global__ void __launch_bounds__(256)
     k_tour_query(TourView h, const int32_t *__restrict__ u, const int32_t *__restrict__ v, int64_t q,
                  int32_t *__restrict__ out, int32_t *__restrict__ status) {
+    pdl_prologue();
     const bool bad_tree = *h.hstatus != 0;
     const int64_t stride = gstride();
     for (int64_t base = gtid(); base < q; base += stride * kIlp) {
@@ -118,7 +120,7 @@ etl_status lca_build_tour_impl(etl_lca_t h, const int32_t *parent, cudaStream_t 
     long long *keys = static_cast<long long *>(h->tour_table);
     {
         PhaseTimer pt("tour_rmq.keys", s);
-        k_tour_keys<<<grid_for(n, 256), 256, 0, s>>>(parent, h->pre, h->depth, h->size, n, keys, h->tpos);
+        launch(k_tour_keys, grid_for(n, 256), 256, 0, s, parent, h->pre, h->depth, h->size, n, keys, h->tpos);
         note_launch();
     }
     etl_status st = last_launch();
@@ -135,7 +137,7 @@ extern "C" etl_status lca_query_tour(etl_lca_t h, const int32_t *u, const int32_
     TourView view{h->n, h->tpos, h->status,
                   blocked_view<OpMinKey>(static_cast<const long long *>(h->tour_table), h->tbl)};
     PhaseTimer pt("tour_rmq.query", s);
-    k_tour_query<<<grid_for(ceil_div(q, kIlp), 256), 256, 0, s>>>(view, u, v, q, out, status);
+    launch(k_tour_query, grid_for(ceil_div(q, kIlp), 256), 256, 0, s, view, u, v, q, out, status);
     note_launch();
     return last_launch();
 }

@@ -4,7 +4,8 @@ The knobs change no result, only speed (``etl_tune_set``): the list ranker's
 splitter densities and walk-kernel shape (threads per block and resident
 blocks per SM of the walks over lists larger than L2), the range tables'
 form and build shape, the radix passes' tile size and ranking, and the
-connectivity pass's hooking schedule. ``autotune`` times candidate settings
+connectivity pass's hooking schedule, and whether kernels are launched as
+programmatic dependents of the one before. ``autotune`` times candidate settings
 with CUDA events on the caller's own work -- a callable that enqueues one
 representative run (for example one batch of trees and graphs of the mix to
 be served), with its inputs already on the device -- and keeps the fastest.
@@ -42,6 +43,7 @@ SPACE = [
     ("rmq_blocked", [0, 1]),
     ("sort_rounds", [8, 16]),
     ("sort_ballot", [0, 1]),
+    ("pdl", [0, 1]),
 ]
 
 

@@ -81,9 +81,9 @@ def test_host_side_validation(lib):
     v = ctypes.c_int32(0)
     assert lib.etl_tune_get(999, ctypes.byref(v)) == 1
     assert lib.etl_tune_set(999, 1) == 1
-    for key, bad in ((1, 0), (1, 9), (3, 100), (5, 4), (7, 0), (8, 2), (9, 12), (12, 2)):
+    for key, bad in ((1, 0), (1, 9), (3, 100), (5, 4), (7, 0), (8, 2), (9, 12), (12, 2), (13, 2)):
         assert lib.etl_tune_set(key, bad) == 1, (key, bad)
-    for key in range(1, 13):  # every key reads back, and writing back its value is accepted
+    for key in range(1, 14):  # every key reads back, and writing back its value is accepted
         assert lib.etl_tune_get(key, ctypes.byref(v)) == 0
         assert lib.etl_tune_set(key, v.value) == 0
 
