@@ -47,6 +47,7 @@ SMALL_GRAPHS = [("easy", 1 << 14, 1 << 17), ("hard", 1 << 14, (1 << 14) - 1 + (1
 # algorithmic bytes of the whole LCA path per node (blocked table) and per query (the per-step byte model)
 LCA_PREPROCESS_BYTES_PER_NODE = 140
 LCA_QUERY_BYTES = 40
+E2E_MIN_STEPS = 60  # steps of the end-to-end measurement (at least --steps)
 
 # algorithmic bytes per unit for each phase (what the method must read and write
 # once: int32 = 4 B); keys are (phase, part) where part is "tree" or "graph"
@@ -726,25 +727,29 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
 
     host_s = []
 
-    def timed(one):
+    def timed(one, steps):
         for _ in range(max(1, args.warmup)):
             one()
         torch.cuda.synchronize()
         host_s.clear()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         evs[0].record(stream)
-        for i in range(args.steps):
+        for i in range(steps):
             h0 = time.perf_counter()
             one()
             host_s.append(time.perf_counter() - h0)
             evs[i + 1].record(stream)
         torch.cuda.synchronize()
-        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-        return evs[0].elapsed_time(evs[-1]) / 1e3 / args.steps, per
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+        return evs[0].elapsed_time(evs[-1]) / 1e3 / steps, per
 
-    t_seq, _ = timed(one_sequential)
+    # at least E2E_MIN_STEPS steps: on some boxes one step in a few dozen takes tens of ms longer (the
+    # device-resident graph replays never do), and the mean over more steps weighs such a pause as
+    # often as it occurs instead of by the luck of a short run
+    e2e_steps = max(args.steps, E2E_MIN_STEPS)
+    t_seq, _ = timed(one_sequential, args.steps)
     t_seq = max_over_ranks(t_seq, world, dev)
-    t, per_step = timed(one_pipelined)
+    t, per_step = timed(one_pipelined, e2e_steps)
     t = max_over_ranks(t, world, dev)
     # copy bandwidth alone, for context: every input of a step in, every result out, nothing else
     dsts = [torch.empty_like(x[k], device=dev) for _, x in jobs for k in ("parent", "u", "v", "edges") if k in x]
@@ -760,7 +765,7 @@ def run_e2e(args, etl, trees, graphs, dev, units, world):
     h2d_s = a.elapsed_time(b) / 1e3 / 3
     del dsts
     return {"value": units * world / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": t * 1e3, "sequential_ms_per_step": t_seq * 1e3,
+            "ms_per_step": t * 1e3, "steps": e2e_steps, "sequential_ms_per_step": t_seq * 1e3,
             "step_ms_min_median_max": [min(per_step), statistics.median(per_step), max(per_step)],
             "step_ms": per_step,
             "host_enqueue_ms_per_step": 1e3 * statistics.median(host_s),
